@@ -1,0 +1,159 @@
+/*
+ * gbhegv.h -- C-ABI of libgbhegv: a GB300 (sm_103a) solver for the
+ * Hermitian-definite generalized eigenproblem  A x = lambda B x  in complex128,
+ * following the paper's Algorithm 1 (Cholesky B = L L^H, reduction
+ * A' = L^{-1} A L^{-H}, standard eigensolver, x = L^{-H} y) with Algorithm 2 in
+ * its two-stage form (Section 4.2: dense -> band -> tridiagonal, tridiagonal
+ * divide and conquer of Section 4.3, back-transformation y = Q1 Q2 y').
+ *
+ * Common conventions
+ *   - complex numbers are gbhe_cplx {re, im} (layout of double2,
+ *     cuDoubleComplex, C99 double complex, torch.complex128);
+ *   - matrices are column-major with a leading dimension (ld >= max(1, rows));
+ *     Hermitian inputs are read from their LOWER triangle only;
+ *   - every matrix/vector pointer is DEVICE memory owned by the caller; the
+ *     library never allocates inside a stream-ordered call: temporaries come
+ *     from the workspace the caller attaches with gbhe_set_workspace;
+ *   - `stream` is a cudaStream_t passed as void*; calls are asynchronous on it;
+ *   - return value: 0 = enqueued (or done), -i = argument i is invalid
+ *     (LAPACK convention, 1-based over the C argument list), GBHE_E* for
+ *     library errors detected on the host.  Numerical failures found on the
+ *     device (B not positive definite, non-convergence, a bounded device wait
+ *     that expired) are recorded in the handle's status word and returned by
+ *     gbhe_get_status, which synchronises the stream.
+ */
+#ifndef GBHEGV_H_
+#define GBHEGV_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double re, im;
+} gbhe_cplx;
+
+typedef struct gbhe_ctx* gbhe_handle;
+
+/* Library error codes (negative values below -100 so they never collide with
+ * the -i argument codes). */
+#define GBHE_EWORKSPACE (-101) /* workspace missing or smaller than gbhe_workspace_size */
+#define GBHE_ECUDA (-102)      /* a CUDA runtime call failed */
+#define GBHE_ETIMEOUT (-103)   /* a bounded device-side wait expired (status word) */
+#define GBHE_ENONFINITE (-104) /* NaN/Inf met where a finite value is required */
+#define GBHE_ENOTCONV (-105)   /* an iteration did not converge (status word) */
+
+/* Create a handle on CUDA device `device` (made current).  Allocates only the
+ * handle's small status buffer.  Returns 0 or GBHE_ECUDA. */
+int gbhe_create(gbhe_handle* handle, int device);
+
+/* Release the handle (does not touch the caller's workspace). */
+int gbhe_destroy(gbhe_handle handle);
+
+/* Bytes of device workspace that every entry point below needs for a
+ * problem of order n, band width nb and m = iu-il+1 wanted eigenvectors
+ * (an upper bound over all stages).  nb = 0 means the default band width. */
+int gbhe_workspace_size(gbhe_handle handle, int n, int nb, int m, size_t* bytes);
+
+/* Attach caller-owned device workspace (256-byte aligned). */
+int gbhe_set_workspace(gbhe_handle handle, void* dwork, size_t bytes);
+
+/* Synchronise `stream` and return the device status: 0 = success,
+ * k > 0 = the leading minor of order k of B is not positive definite
+ * (potrf), or GBHE_ETIMEOUT / GBHE_ENOTCONV.  Clears the status. */
+int gbhe_get_status(gbhe_handle handle, void* stream);
+
+/* Default band width used when nb = 0 is passed. */
+int gbhe_default_nb(int n);
+
+/* Algorithm 1, step 1 (paper Section 3): Cholesky factorisation B = L L^H.
+ * B (n x n, ldb) lower triangle read; L overwrites it (upper untouched).
+ * A non-positive pivot at order k sets status k (first failure wins). */
+int gbhe_potrf(gbhe_handle h, int n, gbhe_cplx* B, int ldb, void* stream);
+
+/* Algorithm 1, step 2: A' = L^{-1} A L^{-H}.  A (n x n, lda) lower triangle
+ * read; on return A holds the full Hermitian A' (both triangles).  L is the
+ * lower factor from gbhe_potrf (n x n, ldl, lower read). */
+int gbhe_hegst(gbhe_handle h, int n, gbhe_cplx* A, int lda, const gbhe_cplx* L, int ldl,
+               void* stream);
+
+/* Algorithm 2, step 1, first stage (Section 4.2, Figure 1): reduction of the
+ * Hermitian A (lower read) to Hermitian band form of half-bandwidth nb,
+ * A = Q1 Band Q1^H.  Block reflectors: panel p (columns p*nb .. p*nb+nb-1)
+ * contributes Q1_p = I - V_p T_p V_p^H acting on rows p*nb+nb .. n-1.
+ * On return the lower band (rows i..i+nb of column i) of A holds the band;
+ * V_p is stored below the band (unit diagonal implicit); T1 receives the
+ * nb x nb upper-triangular T_p of each panel (T1 + p*nb*nb, ld nb; size
+ * ceil(n/nb)*nb*nb); tau1 (n) the reflector scalars.  1 <= nb <= 128. */
+int gbhe_he2hb(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* T1,
+               gbhe_cplx* tau1, void* stream);
+
+/* Size (elements) of the V2 and tau2 arrays of gbhe_hb2st:
+ * V2: n * ceil((n-1)/nb) * nb complex,  tau2: n * ceil((n-1)/nb) complex. */
+int gbhe_hb2st_sizes(int n, int nb, size_t* v2_elems, size_t* tau2_elems);
+
+/* Algorithm 2, step 1, second stage (Section 4.2): bulge chasing with
+ * column-wise elimination from band (lower band of A, half-bandwidth nb) to
+ * real symmetric tridiagonal T = Q2^H Band Q2.  d (n) and e (n-1) receive
+ * the diagonal and sub-diagonal.  Reflector (s, j) -- sweep s = 0..n-2, step
+ * j -- is H = I - tau v v^H acting on rows s+1+j*nb .. s+nb+j*nb (clipped to
+ * n); v (v[0] = 1) is stored at V2 + (s*J + j)*nb and tau at tau2[s*J + j],
+ * J = ceil((n-1)/nb).  Q2 is the product of all H in generation order
+ * (s major, j minor).  A is not modified. */
+int gbhe_hb2st(gbhe_handle h, int n, int nb, const gbhe_cplx* A, int lda, double* d, double* e,
+               gbhe_cplx* V2, gbhe_cplx* tau2, void* stream);
+
+/* Algorithm 2, step 2 (Section 4.3): divide and conquer eigensolver of the
+ * real symmetric tridiagonal (d, e).  w receives the eigenvalues il..iu
+ * (1-based, inclusive, ascending; m = iu-il+1 values) and Z (n x m, ldz) the
+ * orthonormal eigenvectors; in the last merge only these m vectors are
+ * formed (Section 4.3, last paragraph).  d and e are not modified. */
+int gbhe_stedc(gbhe_handle h, int n, const double* d, const double* e, int il, int iu,
+               double* w, double* Z, int ldz, void* stream);
+
+/* Algorithm 2, step 3 for two stages (Section 4.2): X = Q1 Q2 Z for the m
+ * real columns of Z (n x m, ldz); X (n x m, ldx) complex output.  A, T1
+ * from gbhe_he2hb; V2, tau2 from gbhe_hb2st. */
+int gbhe_unmtr_2stage(gbhe_handle h, int n, int nb, int m, const gbhe_cplx* A, int lda,
+                      const gbhe_cplx* T1, const gbhe_cplx* V2, const gbhe_cplx* tau2,
+                      const double* Z, int ldz, gbhe_cplx* X, int ldx, void* stream);
+
+/* Algorithm 1, step 4: X := L^{-H} X for the m columns of X (n x m, ldx);
+ * L lower (n x n, ldl) from gbhe_potrf. */
+int gbhe_trsm_lh(gbhe_handle h, int n, int m, const gbhe_cplx* L, int ldl, gbhe_cplx* X,
+                 int ldx, void* stream);
+
+/* Full two-stage driver (Algorithm 1 around two-stage Algorithm 2):
+ * eigenpairs il..iu (1-based, inclusive) of A x = lambda B x.  A (lower
+ * read) and B (lower read) are overwritten (A by band/V1 data, B by L);
+ * w (m) ascending eigenvalues, X (n x m, ldx) B-orthonormal eigenvectors.
+ * nb = 0 selects the default band width. */
+int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il,
+              int iu, double* w, gbhe_cplx* X, int ldx, void* stream);
+
+/* One-stage comparator (Section 4.1): same contract as gbhe_hegv with the
+ * reduction done by one-stage Householder tridiagonalisation (half of its
+ * flops in Hermitian matrix-vector products) and a single back-transform. */
+int gbhe_hegv_onestage(gbhe_handle h, int n, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il,
+                       int iu, double* w, gbhe_cplx* X, int ldx, void* stream);
+
+/* The FP64 tensor-core (DMMA) GEMM that every level-3 step above uses,
+ * exposed for testing and profiling:  C = alpha op(A) op(B) + beta C, complex128
+ * column-major.  opA in {0: N, 1: T, 2: C (conjugate transpose), 3: Hermitian
+ * matrix read from its lower triangle}; opB in {0: N, 1: T, 2: C}.  lower != 0
+ * writes only C(i,j) with i >= j.  Not part of Algorithms 1-2; the paper has
+ * no counterpart beyond "level 3 BLAS on the GPU" (Section 3). */
+int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const gbhe_cplx* A,
+               int lda, const gbhe_cplx* B, int ldb, gbhe_cplx beta, gbhe_cplx* C, int ldc, int lower,
+               void* stream);
+
+/* Human-readable text for a return/status code. */
+const char* gbhe_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBHEGV_H_ */

@@ -1,0 +1,358 @@
+// api.cu -- the C-ABI of libgbhegv (declared in include/gbhegv.h): handle,
+// workspace, argument checks, per-stage entry points and the drivers.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include "internal.cuh"
+
+using namespace gbhe;
+
+namespace {
+
+int default_nb(int n) {
+  if (n <= 128) return 16;
+  if (n <= 1024) return 32;
+  return 64;
+}
+
+// Workspace every call carves first: split-K scratch and the diagonal-block
+// inverses.
+size_t common_bytes(int n) { return GEMM_SCRATCH_BYTES + dense_ws_bytes(n) + 512; }
+
+size_t stage_bytes(gbhe_handle h, int n, int nb, int m) {
+  size_t s = 0;
+  s = std::max(s, he2hb_ws_bytes(n, nb, h->num_sms));
+  s = std::max(s, hb2st_ws_bytes(n, nb));
+  s = std::max(s, stedc_ws_bytes(n));
+  s = std::max(s, unmtr_ws_bytes(n, nb, m));
+  s = std::max(s, onestage_ws_bytes(n, m));
+  return s;
+}
+
+// Outputs of the intermediate stages that the driver keeps in the workspace.
+size_t driver_bytes(int n, int nb, int m) {
+  const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max(m, 1);
+  const size_t npan = (nn + nb - 1) / nb;
+  const size_t J = (size_t)std::max(hb2st_J(n, nb), 1);
+  size_t b = 0;
+  b += npan * nb * nb * sizeof(cplx) + 256;  // T1
+  b += nn * sizeof(cplx) + 256;              // tau1
+  b += nn * J * nb * sizeof(cplx) + 256;     // V2
+  b += nn * J * sizeof(cplx) + 256;          // tau2
+  b += 2 * nn * sizeof(double) + 512;        // d, e
+  b += nn * mm * sizeof(double) + 256;       // Z
+  return b;
+}
+
+int make_ctx(gbhe_handle h, int n, void* stream, Ctx* c) {
+  if (!h) return GBHE_EWORKSPACE;
+  if (!h->work) return GBHE_EWORKSPACE;
+  c->st = reinterpret_cast<cudaStream_t>(stream);
+  c->status = h->status;
+  c->num_sms = h->num_sms;
+  c->arena.base = reinterpret_cast<char*>(h->work);
+  c->arena.cap = h->work_bytes;
+  c->arena.off = 0;
+  c->arena.measure = false;
+  c->gemm_scratch = c->arena.take<char>(GEMM_SCRATCH_BYTES);
+  c->gemm_scratch_bytes = GEMM_SCRATCH_BYTES;
+  c->dense_scratch = c->arena.take<cplx>(dense_ws_bytes(n) / sizeof(cplx));
+  if (!c->arena.ok() || !c->gemm_scratch) return GBHE_EWORKSPACE;
+  if (cudaSetDevice(h->device) != cudaSuccess) return GBHE_ECUDA;
+  return 0;
+}
+
+inline cplx* Z_(gbhe_cplx* p) { return reinterpret_cast<cplx*>(p); }
+inline const cplx* Z_(const gbhe_cplx* p) { return reinterpret_cast<const cplx*>(p); }
+
+}  // namespace
+
+extern "C" {
+
+int gbhe_default_nb(int n) { return default_nb(n); }
+
+int gbhe_create(gbhe_handle* handle, int device) {
+  if (!handle) return -1;
+  *handle = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return GBHE_ECUDA;
+  gbhe_ctx* h = new gbhe_ctx();
+  h->device = device;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) { delete h; return GBHE_ECUDA; }
+  h->num_sms = p.multiProcessorCount;
+  h->smem_optin = p.sharedMemPerBlockOptin;
+  if (cudaMalloc(&h->status, ST_WORDS * sizeof(int)) != cudaSuccess) { delete h; return GBHE_ECUDA; }
+  if (cudaMemset(h->status, 0, ST_WORDS * sizeof(int)) != cudaSuccess) { cudaFree(h->status); delete h; return GBHE_ECUDA; }
+  if (cudaMallocHost(&h->status_host, ST_WORDS * sizeof(int)) != cudaSuccess) {
+    cudaFree(h->status); delete h; return GBHE_ECUDA;
+  }
+  h->work = nullptr;
+  h->work_bytes = 0;
+  h->spin_limit = 0;
+  *handle = h;
+  return 0;
+}
+
+int gbhe_destroy(gbhe_handle h) {
+  if (!h) return 0;
+  cudaSetDevice(h->device);
+  cudaFree(h->status);
+  cudaFreeHost(h->status_host);
+  delete h;
+  return 0;
+}
+
+int gbhe_workspace_size(gbhe_handle h, int n, int nb, int m, size_t* bytes) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nb == 0) nb = default_nb(n);
+  if (nb < 1 || nb > 128) return -3;
+  if (m < 0 || m > n) return -4;
+  if (!bytes) return -5;
+  *bytes = common_bytes(n) + driver_bytes(n, nb, m) + stage_bytes(h, n, nb, m) + 4096;
+  return 0;
+}
+
+int gbhe_set_workspace(gbhe_handle h, void* dwork, size_t bytes) {
+  if (!h) return -1;
+  if (dwork && (reinterpret_cast<uintptr_t>(dwork) & 255)) return -2;
+  h->work = dwork;
+  h->work_bytes = dwork ? bytes : 0;
+  return 0;
+}
+
+int gbhe_get_status(gbhe_handle h, void* stream) {
+  if (!h) return -1;
+  cudaSetDevice(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GBHE_ECUDA;
+  if (cudaMemcpy(h->status_host, h->status, ST_WORDS * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return GBHE_ECUDA;
+  int info = h->status_host[ST_INFO], err = h->status_host[ST_ERR];
+  if (info != 0 || err != 0)
+    if (cudaMemset(h->status, 0, ST_WORDS * sizeof(int)) != cudaSuccess) return GBHE_ECUDA;
+  if (info > 0) return info;
+  return err;
+}
+
+const char* gbhe_status_string(int code) {
+  switch (code) {
+    case 0: return "success";
+    case GBHE_EWORKSPACE: return "workspace missing or too small";
+    case GBHE_ECUDA: return "CUDA runtime error";
+    case GBHE_ETIMEOUT: return "bounded device wait expired";
+    case GBHE_ENONFINITE: return "non-finite value";
+    case GBHE_ENOTCONV: return "iteration did not converge";
+    default: break;
+  }
+  if (code > 0) return "leading minor of B not positive definite";
+  return "invalid argument";
+}
+
+int gbhe_potrf(gbhe_handle h, int n, gbhe_cplx* B, int ldb, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (n > 0 && !B) return -3;
+  if (ldb < std::max(1, n)) return -4;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return potrf_run(c, n, Z_(B), ldb);
+}
+
+int gbhe_hegst(gbhe_handle h, int n, gbhe_cplx* A, int lda, const gbhe_cplx* L, int ldl, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < std::max(1, n)) return -4;
+  if (n > 0 && !L) return -5;
+  if (ldl < std::max(1, n)) return -6;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return hegst_run(c, n, Z_(A), lda, Z_(L), ldl);
+}
+
+int gbhe_he2hb(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* T1, gbhe_cplx* tau1,
+               void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nb < 1 || nb > 128) return -3;
+  if (n > 0 && !A) return -4;
+  if (lda < std::max(1, n)) return -5;
+  if (n > 0 && !T1) return -6;
+  if (n > 0 && !tau1) return -7;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return he2hb_run(c, n, nb, Z_(A), lda, Z_(T1), Z_(tau1));
+}
+
+int gbhe_hb2st_sizes(int n, int nb, size_t* v2_elems, size_t* tau2_elems) {
+  if (n < 0) return -1;
+  if (nb < 1 || nb > 128) return -2;
+  const size_t J = (size_t)hb2st_J(n, nb);
+  if (v2_elems) *v2_elems = (size_t)n * J * nb;
+  if (tau2_elems) *tau2_elems = (size_t)n * J;
+  return 0;
+}
+
+int gbhe_hb2st(gbhe_handle h, int n, int nb, const gbhe_cplx* A, int lda, double* d, double* e, gbhe_cplx* V2,
+               gbhe_cplx* tau2, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nb < 1 || nb > 128) return -3;
+  if (n > 0 && !A) return -4;
+  if (lda < std::max(1, n)) return -5;
+  if (n > 0 && !d) return -6;
+  if (n > 1 && !e) return -7;
+  if (n > 1 && (!V2 || !tau2)) return -8;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return hb2st_run(c, n, nb, Z_(A), lda, d, e, Z_(V2), Z_(tau2));
+}
+
+int gbhe_stedc(gbhe_handle h, int n, const double* d, const double* e, int il, int iu, double* w, double* Z,
+               int ldz, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (n > 0 && !d) return -3;
+  if (n > 1 && !e) return -4;
+  if (n > 0 && (il < 1 || il > n)) return -5;
+  if (n > 0 && (iu < il || iu > n)) return -6;
+  if (n > 0 && !w) return -7;
+  if (n > 0 && !Z) return -8;
+  if (ldz < std::max(1, n)) return -9;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return stedc_run(c, n, d, e, il, iu, w, Z, ldz);
+}
+
+int gbhe_unmtr_2stage(gbhe_handle h, int n, int nb, int m, const gbhe_cplx* A, int lda, const gbhe_cplx* T1,
+                      const gbhe_cplx* V2, const gbhe_cplx* tau2, const double* Z, int ldz, gbhe_cplx* X, int ldx,
+                      void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nb < 1 || nb > 128) return -3;
+  if (m < 0) return -4;
+  if (n > 0 && !A) return -5;
+  if (lda < std::max(1, n)) return -6;
+  if (n > 0 && !T1) return -7;
+  if (n > 1 && !V2) return -8;
+  if (n > 1 && !tau2) return -9;
+  if (n > 0 && m > 0 && !Z) return -10;
+  if (ldz < std::max(1, n)) return -11;
+  if (n > 0 && m > 0 && !X) return -12;
+  if (ldx < std::max(1, n)) return -13;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return unmtr2_run(c, n, nb, m, Z_(A), lda, Z_(T1), Z_(V2), Z_(tau2), Z, ldz, Z_(X), ldx);
+}
+
+int gbhe_trsm_lh(gbhe_handle h, int n, int m, const gbhe_cplx* L, int ldl, gbhe_cplx* X, int ldx, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (m < 0) return -3;
+  if (n > 0 && !L) return -4;
+  if (ldl < std::max(1, n)) return -5;
+  if (n > 0 && m > 0 && !X) return -6;
+  if (ldx < std::max(1, n)) return -7;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return trsm_run(c, 1, n, m, Z_(L), ldl, Z_(X), ldx);
+}
+
+int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il, int iu,
+              double* w, gbhe_cplx* X, int ldx, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nb == 0) nb = default_nb(n);
+  if (nb < 1 || nb > 128) return -3;
+  if (n > 0 && !A) return -4;
+  if (lda < std::max(1, n)) return -5;
+  if (n > 0 && !B) return -6;
+  if (ldb < std::max(1, n)) return -7;
+  if (n > 0 && (il < 1 || il > n)) return -8;
+  if (n > 0 && (iu < il || iu > n)) return -9;
+  if (n > 0 && !w) return -10;
+  if (n > 0 && !X) return -11;
+  if (ldx < std::max(1, n)) return -12;
+  if (n == 0) return 0;
+  const int m = iu - il + 1;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  Arena& ar = c.arena;
+  const int npan = (n + nb - 1) / nb;
+  const int J = std::max(hb2st_J(n, nb), 1);
+  cplx* T1 = ar.take<cplx>((size_t)npan * nb * nb);
+  cplx* tau1 = ar.take<cplx>((size_t)n);
+  cplx* V2 = ar.take<cplx>((size_t)n * J * nb);
+  cplx* tau2 = ar.take<cplx>((size_t)n * J);
+  double* d = ar.take<double>((size_t)n);
+  double* e = ar.take<double>((size_t)n);
+  double* Z = ar.take<double>((size_t)n * m);
+  if (!ar.ok() || !Z) return GBHE_EWORKSPACE;
+  cplx* Ac = Z_(A);
+  cplx* L = Z_(B);
+  if ((rc = potrf_run(c, n, L, ldb))) return rc;
+  if ((rc = hegst_run(c, n, Ac, lda, L, ldb))) return rc;
+  if ((rc = he2hb_run(c, n, nb, Ac, lda, T1, tau1))) return rc;
+  if ((rc = hb2st_run(c, n, nb, Ac, lda, d, e, V2, tau2))) return rc;
+  if ((rc = stedc_run(c, n, d, e, il, iu, w, Z, n))) return rc;
+  if ((rc = unmtr2_run(c, n, nb, m, Ac, lda, T1, V2, tau2, Z, n, Z_(X), ldx))) return rc;
+  if ((rc = trsm_run(c, 1, n, m, L, ldb, Z_(X), ldx))) return rc;
+  return 0;
+}
+
+int gbhe_hegv_onestage(gbhe_handle h, int n, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il, int iu,
+                       double* w, gbhe_cplx* X, int ldx, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < std::max(1, n)) return -4;
+  if (n > 0 && !B) return -5;
+  if (ldb < std::max(1, n)) return -6;
+  if (n > 0 && (il < 1 || il > n)) return -7;
+  if (n > 0 && (iu < il || iu > n)) return -8;
+  if (n > 0 && !w) return -9;
+  if (n > 0 && !X) return -10;
+  if (ldx < std::max(1, n)) return -11;
+  if (n == 0) return 0;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return hegv_onestage_run(c, n, Z_(A), lda, Z_(B), ldb, il, iu, w, Z_(X), ldx);
+}
+
+int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const gbhe_cplx* A,
+               int lda, const gbhe_cplx* B, int ldb, gbhe_cplx beta, gbhe_cplx* C, int ldc, int lower,
+               void* stream) {
+  if (!h) return -1;
+  if (opA < 0 || opA > 3) return -2;
+  if (opB < 0 || opB > 2) return -3;
+  if (m < 0) return -4;
+  if (n < 0) return -5;
+  if (k < 0) return -6;
+  const int ra = (opA == OP_N || opA == OP_H) ? m : k;
+  if (m > 0 && k > 0 && !A) return -8;
+  if (lda < std::max(1, ra)) return -9;
+  const int rb = (opB == OP_N) ? k : n;
+  if (n > 0 && k > 0 && !B) return -10;
+  if (ldb < std::max(1, rb)) return -11;
+  if (m > 0 && n > 0 && !C) return -13;
+  if (ldc < std::max(1, m)) return -14;
+  if (opA == OP_H && m != k) return -2;
+  Ctx c;
+  int rc = make_ctx(h, 1, stream, &c);
+  if (rc) return rc;
+  return zgemm(c.st, gemm_args(opA, opB, m, n, k, mk(alpha.re, alpha.im), A, lda, B, ldb, mk(beta.re, beta.im), C,
+                               ldc, lower),
+               c.gemm_scratch, c.gemm_scratch_bytes);
+}
+
+}  // extern "C"

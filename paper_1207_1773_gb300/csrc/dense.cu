@@ -1,0 +1,259 @@
+// dense.cu -- Algorithm 1 steps 1, 2 and 4 of the paper (Section 3):
+//   potrf  B = L L^H                (blocked right-looking Cholesky)
+//   hegst  A' = L^{-1} A L^{-H}     (two blocked forward solves)
+//   trsm   X = L^{-1} X  or  X = L^{-H} X
+// The diagonal blocks (DB x DB) are factored / inverted by one CTA each in
+// shared memory; everything else is DMMA GEMM (gemm.cu).
+#include <algorithm>
+#include "internal.cuh"
+
+namespace gbhe {
+namespace {
+
+constexpr int DB = 64;      // diagonal block order
+constexpr int DT = 256;     // threads of the diagonal-block kernels
+
+// Factor the diagonal block A[k0:k0+bs, k0:k0+bs] (lower) in place and write
+// the inverse of its Cholesky factor to Linv (bs x bs, ld DB).
+__global__ void __launch_bounds__(DT) k_potrf_diag(cplx* A, int lda, int k0, int bs, cplx* Linv,
+                                                   int* st) {
+  extern __shared__ cplx sm[];
+  cplx* L = sm;              // DB x DB, ld DB
+  cplx* X = sm + DB * DB;    // inverse
+  const int t = threadIdx.x;
+  for (int i = t; i < bs * bs; i += DT) {
+    int r = i % bs, c = i / bs;
+    L[r + c * DB] = (r >= c) ? A[(size_t)(k0 + r) + (size_t)(k0 + c) * lda] : mk(0.0, 0.0);
+  }
+  __syncthreads();
+  __shared__ double piv;
+  __shared__ int bad;
+  if (t == 0) bad = 0;
+  for (int j = 0; j < bs; ++j) {
+    if (t == 0) {
+      double d = L[j + j * DB].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (!bad) set_info_once(st, k0 + j + 1);
+        bad = 1;
+        d = 1.0;  // keep going on a harmless value; the status word carries the failure
+      }
+      piv = sqrt(d);
+      L[j + j * DB] = mk(piv, 0.0);
+    }
+    __syncthreads();
+    const double inv = 1.0 / piv;
+    for (int r = j + 1 + t; r < bs; r += DT) L[r + j * DB] = cscal(inv, L[r + j * DB]);
+    __syncthreads();
+    // trailing lower update: L[r, c] -= L[r, j] conj(L[c, j]),  j < c <= r
+    const int rem = bs - j - 1;
+    for (int i = t; i < rem * rem; i += DT) {
+      int r = j + 1 + i % rem, c = j + 1 + i / rem;
+      if (r >= c) {
+        cplx a = L[r + c * DB];
+        cplx p = cmulc(L[r + j * DB], L[c + j * DB]);
+        L[r + c * DB] = csub(a, p);
+      }
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular L: column c solved by thread c
+  if (t < bs) {
+    const int c = t;
+    for (int r = 0; r < bs; ++r) {
+      if (r < c) { X[r + c * DB] = mk(0.0, 0.0); continue; }
+      cplx s = mk(r == c ? 1.0 : 0.0, 0.0);
+      for (int q = c; q < r; ++q) s = csub(s, cmul(L[r + q * DB], X[q + c * DB]));
+      X[r + c * DB] = cdiv(s, L[r + r * DB]);
+    }
+  }
+  __syncthreads();
+  for (int i = t; i < bs * bs; i += DT) {
+    int r = i % bs, c = i / bs;
+    if (r >= c) A[(size_t)(k0 + r) + (size_t)(k0 + c) * lda] = L[r + c * DB];
+    Linv[r + c * DB] = X[r + c * DB];
+  }
+}
+
+// Inverse of every diagonal block of the lower-triangular L (block b of order
+// bs_b = min(DB, n - b*DB)) into Linv + b*DB*DB (ld DB).  One CTA per block.
+__global__ void __launch_bounds__(DT) k_trtri_diag(const cplx* Lg, int ldl, int n, cplx* Linv) {
+  extern __shared__ cplx sm[];
+  cplx* L = sm;
+  cplx* X = sm + DB * DB;
+  const int b = blockIdx.x, k0 = b * DB, bs = min(DB, n - k0), t = threadIdx.x;
+  for (int i = t; i < bs * bs; i += DT) {
+    int r = i % bs, c = i / bs;
+    L[r + c * DB] = (r >= c) ? Lg[(size_t)(k0 + r) + (size_t)(k0 + c) * ldl] : mk(0.0, 0.0);
+  }
+  __syncthreads();
+  if (t < bs) {
+    const int c = t;
+    for (int r = 0; r < bs; ++r) {
+      if (r < c) { X[r + c * DB] = mk(0.0, 0.0); continue; }
+      cplx s = mk(r == c ? 1.0 : 0.0, 0.0);
+      for (int q = c; q < r; ++q) s = csub(s, cmul(L[r + q * DB], X[q + c * DB]));
+      X[r + c * DB] = cdiv(s, L[r + r * DB]);
+    }
+  }
+  __syncthreads();
+  cplx* out = Linv + (size_t)b * DB * DB;
+  for (int i = t; i < DB * DB; i += DT) {
+    int r = i % DB, c = i / DB;
+    out[i] = (r < bs && c < bs) ? X[r + c * DB] : mk(0.0, 0.0);
+  }
+}
+
+// Mirror the lower triangle into the upper one (A Hermitian, real diagonal).
+__global__ void k_fill_upper(cplx* A, int lda, int n) {
+  const size_t total = (size_t)n * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(i % n), c = (int)(i / n);
+    if (r < c) A[(size_t)r + (size_t)c * lda] = cconj(A[(size_t)c + (size_t)r * lda]);
+    else if (r == c) A[(size_t)r + (size_t)c * lda].y = 0.0;
+  }
+}
+
+// In-place conjugate transpose of the square n x n A (tiled 32 x 32 swaps).
+__global__ void k_conj_transpose(cplx* A, int lda, int n) {
+  __shared__ cplx t1[32][33], t2[32][33];
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bi < bj) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    int r = bi * 32 + tx, c = bj * 32 + k;
+    if (r < n && c < n) t1[k][tx] = A[(size_t)r + (size_t)c * lda];
+    r = bj * 32 + tx; c = bi * 32 + k;
+    if (r < n && c < n) t2[k][tx] = A[(size_t)r + (size_t)c * lda];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    // element (bj*32+tx, bi*32+k) <- conj(old (bi*32+k, bj*32+tx)) = conj(t1[tx][k])
+    int r = bj * 32 + tx, c = bi * 32 + k;
+    if (r < n && c < n) A[(size_t)r + (size_t)c * lda] = cconj(t1[tx][k]);
+    r = bi * 32 + tx; c = bj * 32 + k;
+    if (bi != bj && r < n && c < n) A[(size_t)r + (size_t)c * lda] = cconj(t2[tx][k]);
+  }
+}
+
+// A := (Y + Y^H)/2 for the square Y stored in A (both triangles written).
+__global__ void k_hermitize(cplx* A, int lda, int n) {
+  const size_t total = (size_t)n * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(i % n), c = (int)(i / n);
+    if (r < c) continue;
+    cplx a = A[(size_t)r + (size_t)c * lda], b = A[(size_t)c + (size_t)r * lda];
+    cplx v = mk(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    if (r == c) v.y = 0.0;
+    A[(size_t)r + (size_t)c * lda] = v;
+    A[(size_t)c + (size_t)r * lda] = cconj(v);
+  }
+}
+
+int diag_smem() { return 2 * DB * DB * (int)sizeof(cplx); }
+
+int ensure_attrs() {
+  static bool done = false;
+  if (done) return 0;
+  GBHE_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, diag_smem()));
+  GBHE_CUDA(cudaFuncSetAttribute(k_trtri_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, diag_smem()));
+  done = true;
+  return 0;
+}
+
+inline int grid1d(size_t total, int threads = 256) {
+  return (int)std::min<size_t>((total + threads - 1) / threads, 152 * 16);
+}
+
+}  // namespace
+
+size_t dense_ws_bytes(int n) {
+  size_t nblk = (size_t)(n + DB - 1) / DB;
+  return nblk * DB * DB * sizeof(cplx) + 256;
+}
+
+int potrf_run(Ctx& c, int n, cplx* B, int ldb) {
+  if (n <= 0) return 0;
+  int rc = ensure_attrs();
+  if (rc) return rc;
+  cplx* Linv = c.dense_scratch;
+  for (int k0 = 0; k0 < n; k0 += DB) {
+    const int bs = std::min(DB, n - k0);
+    k_potrf_diag<<<1, DT, diag_smem(), c.st>>>(B, ldb, k0, bs, Linv, c.status);
+    GBHE_CUDA(cudaGetLastError());
+    const int rest = n - k0 - bs;
+    if (rest <= 0) break;
+    cplx* A21 = B + (size_t)(k0 + bs) + (size_t)k0 * ldb;
+    // L21 = A21 * Linv^H   (in place: one 64-wide column block per CTA row)
+    rc = zgemm(c.st, gemm_args(OP_N, OP_C, rest, bs, bs, mk(1, 0), A21, ldb, Linv, DB, mk(0, 0), A21, ldb),
+               nullptr, 0);
+    if (rc) return rc;
+    // A22 -= L21 L21^H (lower)
+    cplx* A22 = B + (size_t)(k0 + bs) + (size_t)(k0 + bs) * ldb;
+    rc = zgemm(c.st, gemm_args(OP_N, OP_C, rest, rest, bs, mk(-1, 0), A21, ldb, A21, ldb, mk(1, 0), A22, ldb, 1),
+               c.gemm_scratch, c.gemm_scratch_bytes);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+// X (n x m) := L^{-1} X (trans = 0) or L^{-H} X (trans = 1).
+int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, int ldx) {
+  if (n <= 0 || m <= 0) return 0;
+  int rc = ensure_attrs();
+  if (rc) return rc;
+  const int nblk = (n + DB - 1) / DB;
+  cplx* Linv = c.dense_scratch;
+  k_trtri_diag<<<nblk, DT, diag_smem(), c.st>>>(L, ldl, n, Linv);
+  GBHE_CUDA(cudaGetLastError());
+  if (trans == 0) {
+    for (int b = 0; b < nblk; ++b) {
+      const int k0 = b * DB, bs = std::min(DB, n - k0);
+      cplx* Xb = X + k0;
+      rc = zgemm(c.st, gemm_args(OP_N, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
+                                 mk(0, 0), Xb, ldx), nullptr, 0);
+      if (rc) return rc;
+      const int rest = n - k0 - bs;
+      if (rest > 0) {
+        rc = zgemm(c.st, gemm_args(OP_N, OP_N, rest, m, bs, mk(-1, 0), L + (size_t)(k0 + bs) + (size_t)k0 * ldl, ldl,
+                                   Xb, ldx, mk(1, 0), X + k0 + bs, ldx), nullptr, 0);
+        if (rc) return rc;
+      }
+    }
+  } else {
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int k0 = b * DB, bs = std::min(DB, n - k0);
+      cplx* Xb = X + k0;
+      rc = zgemm(c.st, gemm_args(OP_C, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
+                                 mk(0, 0), Xb, ldx), nullptr, 0);
+      if (rc) return rc;
+      if (k0 > 0) {
+        // X[0:k0] -= L[k0:k0+bs, 0:k0]^H X_b
+        rc = zgemm(c.st, gemm_args(OP_C, OP_N, k0, m, bs, mk(-1, 0), L + k0, ldl, Xb, ldx, mk(1, 0), X, ldx),
+                   nullptr, 0);
+        if (rc) return rc;
+      }
+    }
+  }
+  return 0;
+}
+
+int hegst_run(Ctx& c, int n, cplx* A, int lda, const cplx* L, int ldl) {
+  if (n <= 0) return 0;
+  const size_t total = (size_t)n * n;
+  k_fill_upper<<<grid1d(total), 256, 0, c.st>>>(A, lda, n);
+  GBHE_CUDA(cudaGetLastError());
+  int rc = trsm_run(c, 0, n, n, L, ldl, A, lda);  // W = L^{-1} A
+  if (rc) return rc;
+  dim3 tg((n + 31) / 32, (n + 31) / 32);
+  k_conj_transpose<<<tg, dim3(32, 8), 0, c.st>>>(A, lda, n);  // W^H
+  GBHE_CUDA(cudaGetLastError());
+  rc = trsm_run(c, 0, n, n, L, ldl, A, lda);  // L^{-1} W^H = A'^H
+  if (rc) return rc;
+  k_hermitize<<<grid1d(total), 256, 0, c.st>>>(A, lda, n);
+  GBHE_CUDA(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace gbhe

@@ -1,0 +1,226 @@
+// he2hb.cu -- first stage of the two-stage tridiagonalisation (paper Section
+// 4.2, Figure 1): Hermitian dense -> Hermitian band of half-bandwidth nb by
+// block Householder transformations.
+//
+// For each panel (columns k..k+nb-1):
+//   (a) QR of the panel P = A[k+nb:n, k:k+nb] = Q R,  Q = I - V T V^H
+//       (one cooperative kernel: rows split over the CTAs, each CTA keeps its
+//       rows in shared memory; two bounded grid barriers per column);
+//   (c) two-sided update of the trailing matrix A22 <- Q^H A22 Q as
+//       X = A22 V T,  W = X - 1/2 V (T^H V^H X),  A22 -= V W^H + W V^H
+//       (DMMA GEMMs; A22 read as Hermitian from its lower triangle and only
+//       the lower triangle written).
+#include <algorithm>
+#include "internal.cuh"
+
+namespace gbhe {
+namespace {
+
+constexpr int PT = 256;
+
+struct PanelArgs {
+  cplx* A;
+  int lda, n, k, nb, kr, mp, chunk;
+  cplx* V;     // explicit V (mp x nb, ld ldv): unit diagonal, zeros above
+  int ldv;
+  cplx* tau;   // tau1 + k
+  cplx* T;     // nb x nb, ld nb
+  cplx* part;  // G x (nb + 1) partial sums
+  cplx* alpha; // 1 slot
+  unsigned* bar;
+  int* st;
+};
+
+__device__ __forceinline__ cplx warp_sum(cplx v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(PT) k_panel_qr(PanelArgs p) {
+  extern __shared__ cplx S[];  // chunk x nb, ld chunk
+  __shared__ cplx wtot[128];
+  __shared__ cplx red[PT / 32];
+  __shared__ cplx sh_tau, sh_scal;
+  __shared__ double sh_beta;
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int r0 = b * p.chunk, r1 = min(p.mp, r0 + p.chunk), rows = max(0, r1 - r0);
+  const int nb = p.nb, PS = nb + 1;
+  for (int i = t; i < rows * nb; i += PT) {
+    int r = i % rows, c = i / rows;
+    S[r + c * p.chunk] = p.A[(size_t)(p.k + nb + r0 + r) + (size_t)(p.k + c) * p.lda];
+  }
+  if (b == 0)
+    for (int i = t; i < nb * nb; i += PT) p.T[i] = mk(0.0, 0.0);
+  __syncthreads();
+
+  for (int j = 0; j < p.kr; ++j) {
+    // ---- phase 1: partial |x|^2 below the diagonal of column j
+    double s = 0.0;
+    for (int r = t; r < rows; r += PT) {
+      int gi = r0 + r;
+      if (gi > j) s += cabs2(S[r + j * p.chunk]);
+    }
+    cplx sv = warp_sum(mk(s, 0.0));
+    if (lane == 0) red[warp] = sv;
+    __syncthreads();
+    if (t == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < PT / 32; ++w) tot += red[w].x;
+      p.part[(size_t)b * PS] = mk(tot, 0.0);
+      if (j >= r0 && j < r1) *p.alpha = S[(j - r0) + j * p.chunk];
+    }
+    if (!grid_barrier(p.bar, G, p.st)) return;
+    // ---- phase 2: reflector, scale v, partial sums of V^H v_j and v_j^H P
+    if (warp == 0) {
+      double x2 = 0.0;
+      for (int q = lane; q < G; q += 32) x2 += __ldcg(&p.part[(size_t)q * PS]).x;
+      cplx tt = warp_sum(mk(x2, 0.0));
+      if (lane == 0) {
+        cplx al = __ldcg(p.alpha);
+        double xn2 = tt.x;
+        if (xn2 == 0.0 && al.y == 0.0) {
+          sh_tau = mk(0.0, 0.0); sh_beta = al.x; sh_scal = mk(0.0, 0.0);
+        } else {
+          double nrm = sqrt(al.x * al.x + al.y * al.y + xn2);
+          double beta = (al.x >= 0.0) ? -nrm : nrm;
+          sh_beta = beta;
+          sh_tau = mk((beta - al.x) / beta, -al.y / beta);
+          sh_scal = cinv(mk(al.x - beta, al.y));
+        }
+      }
+    }
+    __syncthreads();
+    const cplx tau = sh_tau, scal = sh_scal;
+    for (int r = t; r < rows; r += PT) {
+      int gi = r0 + r;
+      if (gi > j) S[r + j * p.chunk] = cmul(S[r + j * p.chunk], scal);
+      else if (gi == j) S[r + j * p.chunk] = mk(sh_beta, 0.0);
+    }
+    if (b == 0 && t == 0) p.tau[j] = tau;
+    __syncthreads();
+    for (int c = warp; c < nb; c += PT / 32) {
+      if (c == j) continue;
+      cplx acc = mk(0.0, 0.0);
+      for (int r = lane; r < rows; r += 32) {
+        int gi = r0 + r;
+        if (gi < j) continue;
+        cplx vj = (gi == j) ? mk(1.0, 0.0) : S[r + j * p.chunk];
+        if (c < j) ccfma(acc, S[r + c * p.chunk], vj);      // conj(V(i,c)) v_j(i)
+        else ccfma(acc, vj, S[r + c * p.chunk]);            // conj(v_j(i)) P(i,c)
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) p.part[(size_t)b * PS + 1 + c] = acc;
+    }
+    if (!grid_barrier(p.bar, G, p.st)) return;
+    // ---- phase 3: totals, update of the remaining columns, T column j
+    for (int c = warp; c < nb; c += PT / 32) {
+      cplx acc = mk(0.0, 0.0);
+      if (c != j)
+        for (int q = lane; q < G; q += 32) acc = cadd(acc, __ldcg(&p.part[(size_t)q * PS + 1 + c]));
+      acc = warp_sum(acc);
+      if (lane == 0) wtot[c] = acc;
+    }
+    __syncthreads();
+    const cplx ctau = cconj(tau);
+    for (int i = t; i < rows * nb; i += PT) {
+      int r = i % rows, c = i / rows, gi = r0 + r;
+      if (c <= j || gi < j) continue;
+      cplx vj = (gi == j) ? mk(1.0, 0.0) : S[r + j * p.chunk];
+      // P(i,c) -= conj(tau) v_j(i) w_c
+      S[r + c * p.chunk] = csub(S[r + c * p.chunk], cmul(ctau, cmul(vj, wtot[c])));
+    }
+    if (b == 0) {
+      // T(0:j, j) = -tau T(0:j,0:j) (V^H v_j);  T(j,j) = tau
+      for (int r = t; r < j; r += PT) {
+        cplx acc = mk(0.0, 0.0);
+        for (int q = r; q < j; ++q) cfma(acc, p.T[r + q * nb], wtot[q]);
+        p.T[r + j * nb] = cscal(-1.0, cmul(tau, acc));
+      }
+      if (t == 0) p.T[j + j * nb] = tau;
+    }
+    __syncthreads();
+  }
+  // write back the panel (R above/on the diagonal, V below) and explicit V
+  for (int i = t; i < rows * nb; i += PT) {
+    int r = i % rows, c = i / rows, gi = r0 + r;
+    cplx v = S[r + c * p.chunk];
+    p.A[(size_t)(p.k + nb + gi) + (size_t)(p.k + c) * p.lda] = v;
+    cplx e = mk(0.0, 0.0);
+    if (c < p.kr) {
+      if (gi == c) e = mk(1.0, 0.0);
+      else if (gi > c) e = v;
+    }
+    p.V[(size_t)gi + (size_t)c * p.ldv] = e;
+  }
+}
+
+}  // namespace
+
+size_t he2hb_ws_bytes(int n, int nb, int num_sms) {
+  size_t nn = (size_t)std::max(n, 1);
+  size_t b = 0;
+  b += nn * nb * sizeof(cplx) * 3 + 3 * 256;          // V, VT, X
+  b += (size_t)nb * nb * sizeof(cplx) * 2 + 2 * 256;  // Y, Z
+  b += (size_t)(num_sms + 1) * (nb + 1) * sizeof(cplx) + 256;
+  b += 256 * 2;
+  return b;
+}
+
+int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
+  if (n <= 0) return 0;
+  Arena& a = c.arena;
+  const size_t save = a.off;
+  cplx* V = a.take<cplx>((size_t)n * nb);
+  cplx* VT = a.take<cplx>((size_t)n * nb);
+  cplx* X = a.take<cplx>((size_t)n * nb);
+  cplx* Ys = a.take<cplx>((size_t)nb * nb);
+  cplx* Zs = a.take<cplx>((size_t)nb * nb);
+  cplx* part = a.take<cplx>((size_t)(c.num_sms + 1) * (nb + 1));
+  cplx* alpha = a.take<cplx>(1);
+  if (!a.ok() || !V) { a.off = save; return GBHE_EWORKSPACE; }
+  GBHE_CUDA(cudaMemsetAsync(tau1, 0, sizeof(cplx) * n, c.st));
+  const int npan = (n + nb - 1) / nb;
+  GBHE_CUDA(cudaMemsetAsync(T1, 0, sizeof(cplx) * (size_t)npan * nb * nb, c.st));
+  int rc = 0;
+  for (int k = 0; k + nb < n; k += nb) {
+    const int mp = n - k - nb;
+    const int kr = std::min(nb, mp);
+    // ---- panel QR
+    int G = std::min(c.num_sms, std::max(1, (mp + 7) / 8));
+    int chunk = (mp + G - 1) / G;
+    size_t smem = (size_t)chunk * nb * sizeof(cplx);
+    if (smem > 200 * 1024) { a.off = save; return -3; }
+    static size_t attr_set = 0;
+    if (smem > 48 * 1024 && smem > attr_set) {
+      GBHE_CUDA(cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+      attr_set = 210 * 1024;
+    }
+    PanelArgs pa;
+    pa.A = A; pa.lda = lda; pa.n = n; pa.k = k; pa.nb = nb; pa.kr = kr; pa.mp = mp; pa.chunk = chunk;
+    pa.V = V; pa.ldv = n; pa.tau = tau1 + k + 0; pa.T = T1 + (size_t)(k / nb) * nb * nb;
+    pa.part = part; pa.alpha = alpha; pa.bar = reinterpret_cast<unsigned*>(c.status + ST_BAR);
+    pa.st = c.status;
+    void* args[] = {&pa};
+    GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PT), args, smem, c.st));
+    // ---- trailing update
+    cplx* A22 = A + (size_t)(k + nb) + (size_t)(k + nb) * lda;
+    const cplx* T = pa.T;
+    const cplx one = mk(1, 0), zero = mk(0, 0), mone = mk(-1, 0);
+    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, mp, kr, kr, one, V, n, T, nb, zero, VT, n), nullptr, 0))) break;
+    if ((rc = zgemm(c.st, gemm_args(OP_H, OP_N, mp, kr, mp, one, A22, lda, VT, n, zero, X, n), nullptr, 0))) break;
+    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, kr, kr, mp, one, V, n, X, n, zero, Ys, nb), c.gemm_scratch,
+                    c.gemm_scratch_bytes))) break;
+    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, kr, kr, kr, one, T, nb, Ys, nb, zero, Zs, nb), nullptr, 0))) break;
+    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, mp, kr, kr, mk(-0.5, 0), V, n, Zs, nb, one, X, n), nullptr, 0))) break;
+    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_C, mp, mp, kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0))) break;
+    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_C, mp, mp, kr, mone, X, n, V, n, one, A22, lda, 1), nullptr, 0))) break;
+  }
+  a.off = save;
+  return rc;
+}
+
+}  // namespace gbhe

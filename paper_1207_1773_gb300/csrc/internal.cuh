@@ -1,0 +1,46 @@
+// internal.cuh -- per-call context and the stage functions shared by the C-ABI.
+#pragma once
+#include "common.cuh"
+#include "gemm.cuh"
+
+namespace gbhe {
+
+// Everything a stage needs for one call: the stream, the device status words
+// and carved pieces of the caller's workspace.
+struct Ctx {
+  cudaStream_t st;
+  int* status;
+  int num_sms;
+  cplx* dense_scratch;        // diagonal-block inverses, ceil(n/64)*64*64
+  void* gemm_scratch;         // split-K partial sums
+  size_t gemm_scratch_bytes;
+  Arena arena;                // the rest, for stage temporaries
+};
+
+constexpr size_t GEMM_SCRATCH_BYTES = size_t(32) << 20;
+
+size_t dense_ws_bytes(int n);
+int potrf_run(Ctx& c, int n, cplx* B, int ldb);
+int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, int ldx);
+int hegst_run(Ctx& c, int n, cplx* A, int lda, const cplx* L, int ldl);
+
+size_t he2hb_ws_bytes(int n, int nb, int num_sms);
+int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1);
+
+inline int hb2st_J(int n, int nb) { return n > 1 ? (n - 1 + nb - 1) / nb : 0; }
+size_t hb2st_ws_bytes(int n, int nb);
+int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* e, cplx* V2, cplx* tau2);
+
+size_t stedc_ws_bytes(int n);
+int stedc_run(Ctx& c, int n, const double* d, const double* e, int il, int iu, double* w, double* Z,
+              int ldz);
+
+size_t unmtr_ws_bytes(int n, int nb, int m);
+int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx* T1, const cplx* V2,
+               const cplx* tau2, const double* Z, int ldz, cplx* X, int ldx);
+
+size_t onestage_ws_bytes(int n, int m);
+int hegv_onestage_run(Ctx& c, int n, cplx* A, int lda, cplx* B, int ldb, int il, int iu, double* w,
+                      cplx* X, int ldx);
+
+}  // namespace gbhe

@@ -1,0 +1,320 @@
+"""Thin ctypes binding of libgbhegv (C-ABI in include/gbhegv.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library.
+PyTorch provides device memory (tensors, workspace) and streams.  If the
+library is missing this module raises; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libgbhegv.so")
+
+GBHE_EWORKSPACE = -101
+GBHE_ECUDA = -102
+GBHE_ETIMEOUT = -103
+GBHE_ENONFINITE = -104
+GBHE_ENOTCONV = -105
+
+
+class GbheError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__("%s failed: %d (%s)" % (fn, code, status_string(code)))
+
+
+class _Cplx(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIBPATH):
+            raise RuntimeError("libgbhegv.so not built (run __graft_entry__.build() or "
+                               "python paper_1207_1773_gb300/build.py)")
+        lib = ctypes.CDLL(_LIBPATH)
+        P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        sig = {
+            "gbhe_create": ([ctypes.POINTER(P), I], I),
+            "gbhe_destroy": ([P], I),
+            "gbhe_workspace_size": ([P, I, I, I, ctypes.POINTER(S)], I),
+            "gbhe_set_workspace": ([P, P, S], I),
+            "gbhe_get_status": ([P, P], I),
+            "gbhe_default_nb": ([I], I),
+            "gbhe_potrf": ([P, I, P, I, P], I),
+            "gbhe_hegst": ([P, I, P, I, P, I, P], I),
+            "gbhe_he2hb": ([P, I, I, P, I, P, P, P], I),
+            "gbhe_hb2st_sizes": ([I, I, ctypes.POINTER(S), ctypes.POINTER(S)], I),
+            "gbhe_hb2st": ([P, I, I, P, I, P, P, P, P, P], I),
+            "gbhe_stedc": ([P, I, P, P, I, I, P, P, I, P], I),
+            "gbhe_unmtr_2stage": ([P, I, I, I, P, I, P, P, P, P, I, P, I, P], I),
+            "gbhe_trsm_lh": ([P, I, I, P, I, P, I, P], I),
+            "gbhe_hegv": ([P, I, I, P, I, P, I, I, I, P, P, I, P], I),
+            "gbhe_hegv_onestage": ([P, I, P, I, P, I, I, I, P, P, I, P], I),
+            "gbhe_status_string": ([I], ctypes.c_char_p),
+            "gbhe_zgemm": ([P, I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def exported_symbols():
+    return [n for n in ("gbhe_create", "gbhe_destroy", "gbhe_workspace_size", "gbhe_set_workspace",
+                        "gbhe_get_status", "gbhe_default_nb", "gbhe_potrf", "gbhe_hegst", "gbhe_he2hb",
+                        "gbhe_hb2st_sizes", "gbhe_hb2st", "gbhe_stedc", "gbhe_unmtr_2stage",
+                        "gbhe_trsm_lh", "gbhe_hegv", "gbhe_hegv_onestage", "gbhe_status_string",
+                        "gbhe_zgemm")]
+
+
+def status_string(code: int) -> str:
+    return _load().gbhe_status_string(int(code)).decode()
+
+
+def _check(fn, rc):
+    if rc != 0:
+        raise GbheError(fn, rc)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(dev):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+class Handle:
+    """A library handle on one device plus a torch-allocated workspace."""
+
+    def __init__(self, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("gbhegv runs on CUDA devices only")
+        self.device = dev
+        lib = _load()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check("gbhe_create", lib.gbhe_create(ctypes.byref(h), dev.index or 0))
+        self.h = h
+        self.work = None
+        self.work_bytes = 0
+
+    def close(self):
+        if self.h:
+            _load().gbhe_destroy(self.h)
+            self.h = None
+            self.work = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_size(self, n, nb=0, m=None):
+        m = n if m is None else m
+        b = ctypes.c_size_t()
+        _check("gbhe_workspace_size", _load().gbhe_workspace_size(self.h, int(n), int(nb), int(m), ctypes.byref(b)))
+        return int(b.value)
+
+    def ensure_workspace(self, n, nb=0, m=None):
+        need = self.workspace_size(n, nb, m)
+        if self.work is None or self.work_bytes < need:
+            self.work = None
+            torch.cuda.synchronize(self.device)
+            self.work = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self.work_bytes = need
+            _check("gbhe_set_workspace", _load().gbhe_set_workspace(self.h, _ptr(self.work), ctypes.c_size_t(need)))
+        return self.work
+
+    def status(self):
+        return int(_load().gbhe_get_status(self.h, _stream(self.device)))
+
+
+_handles = {}
+
+
+def handle(device=None) -> Handle:
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    key = dev.index or 0
+    if key not in _handles:
+        _handles[key] = Handle(dev)
+    return _handles[key]
+
+
+def _ld(t):
+    """Leading dimension of a column-major 2-D tensor (a transposed row-major view)."""
+    if t.dim() == 1:
+        return max(t.shape[0], 1)
+    if t.stride(0) != 1:
+        raise ValueError("matrices must be column-major (use t.t().contiguous().t() or torch_colmajor)")
+    return max(t.stride(1), t.shape[0], 1)
+
+
+def colmajor(x, device=None, dtype=None):
+    """Column-major copy of a numpy array or tensor on the device."""
+    t = torch.as_tensor(x)
+    if dtype is not None:
+        t = t.to(dtype)
+    if device is not None:
+        t = t.to(device)
+    if t.dim() == 2:
+        return t.t().contiguous().t()
+    return t.contiguous()
+
+
+def _sync_status(h, fn):
+    st = h.status()
+    if st != 0:
+        raise GbheError(fn, st)
+
+
+# ----------------------------------------------------------------- stages
+def potrf(B, check=True):
+    h = handle(B.device)
+    n = B.shape[0]
+    h.ensure_workspace(n)
+    _check("gbhe_potrf", _load().gbhe_potrf(h.h, n, _ptr(B), _ld(B), _stream(B.device)))
+    return h.status() if check else 0
+
+
+def hegst(A, L):
+    h = handle(A.device)
+    n = A.shape[0]
+    h.ensure_workspace(n)
+    _check("gbhe_hegst", _load().gbhe_hegst(h.h, n, _ptr(A), _ld(A), _ptr(L), _ld(L), _stream(A.device)))
+
+
+def he2hb(A, nb):
+    """Returns (T1, tau1); A is overwritten by band + V1."""
+    h = handle(A.device)
+    n = A.shape[0]
+    h.ensure_workspace(n, nb)
+    npan = max((n + nb - 1) // nb, 1)
+    T1 = torch.zeros(npan * nb * nb, dtype=torch.complex128, device=A.device)
+    tau1 = torch.zeros(max(n, 1), dtype=torch.complex128, device=A.device)
+    _check("gbhe_he2hb", _load().gbhe_he2hb(h.h, n, nb, _ptr(A), _ld(A), _ptr(T1), _ptr(tau1), _stream(A.device)))
+    _sync_status(h, "gbhe_he2hb")
+    return T1, tau1
+
+
+def hb2st_sizes(n, nb):
+    v, t = ctypes.c_size_t(), ctypes.c_size_t()
+    _check("gbhe_hb2st_sizes", _load().gbhe_hb2st_sizes(n, nb, ctypes.byref(v), ctypes.byref(t)))
+    return int(v.value), int(t.value)
+
+
+def hb2st(A, nb):
+    """Returns (d, e, V2, tau2) from the lower band of A."""
+    h = handle(A.device)
+    n = A.shape[0]
+    h.ensure_workspace(n, nb)
+    nv, nt = hb2st_sizes(n, nb)
+    d = torch.zeros(max(n, 1), dtype=torch.float64, device=A.device)
+    e = torch.zeros(max(n, 1), dtype=torch.float64, device=A.device)
+    V2 = torch.zeros(max(nv, 1), dtype=torch.complex128, device=A.device)
+    tau2 = torch.zeros(max(nt, 1), dtype=torch.complex128, device=A.device)
+    _check("gbhe_hb2st", _load().gbhe_hb2st(h.h, n, nb, _ptr(A), _ld(A), _ptr(d), _ptr(e), _ptr(V2), _ptr(tau2),
+                                            _stream(A.device)))
+    _sync_status(h, "gbhe_hb2st")
+    return d[:n], e[:max(n - 1, 0)], V2, tau2
+
+
+def stedc(d, e, il=1, iu=None):
+    """Eigenpairs il..iu of the real symmetric tridiagonal (d, e): (w, Z)."""
+    h = handle(d.device)
+    n = d.shape[0]
+    iu = n if iu is None else iu
+    m = iu - il + 1
+    h.ensure_workspace(n, 0, m)
+    w = torch.zeros(max(m, 1), dtype=torch.float64, device=d.device)
+    Z = torch.zeros((max(m, 1), n), dtype=torch.float64, device=d.device).t()
+    e_ = e if e.numel() > 0 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    _check("gbhe_stedc", _load().gbhe_stedc(h.h, n, _ptr(d), _ptr(e_), il, iu, _ptr(w), _ptr(Z), max(n, 1),
+                                            _stream(d.device)))
+    _sync_status(h, "gbhe_stedc")
+    return w[:m], Z[:, :m]
+
+
+def unmtr_2stage(nb, A, T1, V2, tau2, Z):
+    h = handle(A.device)
+    n, m = Z.shape
+    h.ensure_workspace(n, nb, m)
+    X = torch.zeros((max(m, 1), n), dtype=torch.complex128, device=A.device).t()
+    _check("gbhe_unmtr_2stage", _load().gbhe_unmtr_2stage(h.h, n, nb, m, _ptr(A), _ld(A), _ptr(T1), _ptr(V2),
+                                                          _ptr(tau2), _ptr(Z), _ld(Z), _ptr(X), max(n, 1),
+                                                          _stream(A.device)))
+    _sync_status(h, "gbhe_unmtr_2stage")
+    return X[:, :m]
+
+
+def trsm_lh(L, X):
+    h = handle(L.device)
+    n, m = X.shape
+    h.ensure_workspace(n, 0, m)
+    _check("gbhe_trsm_lh", _load().gbhe_trsm_lh(h.h, n, m, _ptr(L), _ld(L), _ptr(X), _ld(X), _stream(L.device)))
+
+
+OPS = {"N": 0, "T": 1, "C": 2, "H": 3}
+
+
+def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
+    """C = alpha op(A) op(B) + beta C on the library's DMMA GEMM (in place)."""
+    h = handle(C.device)
+    h.ensure_workspace(1)
+    m, n = C.shape
+    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    a, b = complex(alpha), complex(beta)
+    _check("gbhe_zgemm", _load().gbhe_zgemm(h.h, OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag), _ptr(A),
+                                            _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C), _ld(C),
+                                            int(bool(lower)), _stream(C.device)))
+    return C
+
+
+def hegv(A, B, il=1, iu=None, nb=0, onestage=False, check=True):
+    """Eigenpairs il..iu (1-based, inclusive) of A x = lambda B x.
+
+    A, B: column-major complex128 CUDA tensors (lower triangles read), both
+    overwritten.  Returns (w, X) with X B-orthonormal."""
+    h = handle(A.device)
+    n = A.shape[0]
+    iu = n if iu is None else iu
+    m = iu - il + 1
+    nbu = nb if nb else _load().gbhe_default_nb(n)
+    h.ensure_workspace(n, nbu, m)
+    w = torch.zeros(max(m, 1), dtype=torch.float64, device=A.device)
+    X = torch.zeros((max(m, 1), n), dtype=torch.complex128, device=A.device).t()
+    st = _stream(A.device)
+    if onestage:
+        rc = _load().gbhe_hegv_onestage(h.h, n, _ptr(A), _ld(A), _ptr(B), _ld(B), il, iu, _ptr(w), _ptr(X),
+                                        max(n, 1), st)
+        _check("gbhe_hegv_onestage", rc)
+    else:
+        rc = _load().gbhe_hegv(h.h, n, nbu, _ptr(A), _ld(A), _ptr(B), _ld(B), il, iu, _ptr(w), _ptr(X),
+                               max(n, 1), st)
+        _check("gbhe_hegv", rc)
+    if check:
+        _sync_status(h, "gbhe_hegv")
+    return w[:m], X[:, :m]
