@@ -1,0 +1,361 @@
+"""Benchmark: two-stage Hermitian-definite generalized eigensolver on GB300.
+
+Workload (default): n = 10000 complex128 pair A x = lambda B x built with a
+known spectrum (Lambda ~ U[-10, 10], seed 10; B = L L^H, A = L Q Lambda Q^H L^H),
+all n eigenpairs, band width 64.  One step = one full solve through the
+library's C-ABI driver gbhe_hegv (potrf, hegst, he2hb, hb2st, divide and
+conquer, two-stage back-transform, trsm) on inputs already resident in HBM;
+each step starts by restoring A and B from device copies (they are
+overwritten), inside the timed region.
+
+Metric: generalized solve time and GFLOP/s with the fixed nominal count
+N(n, m) = (32/3) n^3 + 12 n^2 m real flops (identical for one- and two-stage).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n 10000] [--frac 1.0] [--nb 64] [--no-e2e] [--no-onestage]
+
+--impl reference times the CPU oracle (plain C, FP64, one-stage) on a bounded
+sample of the same workload (n = 1536) on the host cores.
+Under torchrun (N > 1) every rank solves its own replica (the method does not
+shard across GPUs in this build: replicas only); value = all ranks' flops /
+max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "generalized solve time (s) & GFLOP/s at n=10k complex128 vs one-stage on same GPU"
+UNIT = "GFLOP/s"
+CPU_SAMPLE_N = 1536
+
+
+def nominal_flops(n, m):
+    return 32.0 / 3.0 * n ** 3 + 12.0 * n * n * m
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=10000)
+    p.add_argument("--frac", type=float, default=1.0)
+    p.add_argument("--nb", type=int, default=64)
+    p.add_argument("--seed", type=int, default=10)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-onestage", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1207_1773_gb300 import inputs
+
+    n = CPU_SAMPLE_N
+    m = max(1, inputs.fraction_iu(n, args.frac))
+    A, B, lam = inputs.make_pair(n, args.seed, "uniform", -10.0, 10.0)
+    for _ in range(args.warmup):
+        oracle.hegv(A, B, 1, m)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        w, X, info = oracle.hegv(A, B, 1, m)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    val = nominal_flops(n, m) * args.steps / T / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
+        "data": "synthetic",
+        "config": {"workload": "bounded CPU sample of the n=10000 workload: n=%d complex128 pair, Lambda~U[-10,10], "
+                               "seed %d, lowest %d eigenpairs" % (n, args.seed, m),
+                   "n": n, "m": m, "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "oracle.hegv at n=%d, m=%d (one-stage Householder + implicit QR)" % (n, m)},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "max_abs_eig_err": float(np.max(np.abs(w - lam[:m]))),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1207_1773_gb300 import gbhegv as G
+    from paper_1207_1773_gb300 import inputs
+
+    n = args.n
+    m = max(1, inputs.fraction_iu(n, args.frac))
+    nb = args.nb
+    t0 = time.time()
+    A_np, B_np, lam = inputs.make_pair(n, args.seed + rank, "uniform", -10.0, 10.0,
+                                       device=dev if n > 3000 else None)
+    gen_s = time.time() - t0
+    A0 = G.colmajor(A_np, dev)
+    B0 = G.colmajor(B_np, dev)
+    A = torch.empty_like(A0)
+    B = torch.empty_like(B0)
+    h = G.handle(dev)
+    h.ensure_workspace(n, nb, m)
+    dfma_peak, dmma_peak = G.probe_fp64_peaks(dev.index)
+
+    def step(onestage=False):
+        A.copy_(A0)
+        B.copy_(B0)
+        return G.hegv(A, B, 1, m, nb=nb, onestage=onestage, check=False)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    st = h.status()
+    if st != 0:
+        raise RuntimeError("solver status %d during warm-up" % st)
+
+    # ---- timed region (device-resident inputs)
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(dev.index)
+    clocks.start()
+    G.profile_enable(True)
+    launches0 = G.launch_count()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        w, X = step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = G.launch_count() - launches0
+    prof = G.profile_read()
+    G.profile_enable(False)
+    clk = clocks.stop()
+    st = h.status()
+    if st != 0:
+        raise RuntimeError("solver status %d in the timed region" % st)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_flops = nominal_flops(n, m) * args.steps * ws
+    value = total_flops / (ms * 1e-3) / 1e9
+
+    # accuracy of the last timed step against the constructed spectrum
+    w_np = w.cpu().numpy()
+    eig_err = float(np.max(np.abs(w_np - lam[:m])))
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        # pinned, column-major (transposed row-major) like the device copies
+        Ah = torch.empty((n, n), dtype=torch.complex128, pin_memory=True).t()
+        Bh = torch.empty((n, n), dtype=torch.complex128, pin_memory=True).t()
+        Ah.copy_(A0)
+        Bh.copy_(B0)
+        Xh = torch.empty((m, n), dtype=torch.complex128).pin_memory().t()
+        wh = torch.empty(m, dtype=torch.float64).pin_memory()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            A.copy_(Ah, non_blocking=True)
+            B.copy_(Bh, non_blocking=True)
+            w2, X2 = G.hegv(A, B, 1, m, nb=nb, check=False)
+            Xh.copy_(X2, non_blocking=True)
+            wh.copy_(w2, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ms2 = f0.elapsed_time(f1)
+        if dist is not None:
+            t = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        e2e = {"value": total_flops / (ms2 * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(2 * n * n * 16), "d2h_bytes_per_step": int(n * m * 16 + m * 8),
+               "ms_per_step": ms2 / args.steps}
+
+    # ---- one-stage comparator on the same GPU (one untimed warm-up, one timed solve)
+    onestage = None
+    if not args.no_onestage:
+        try:
+            step(onestage=True)
+            barrier()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            w3, _ = step(onestage=True)
+            g1.record(stream)
+            barrier()
+            ms3 = g0.elapsed_time(g1)
+            onestage = {"solve_time_s": ms3 / 1e3, "value": nominal_flops(n, m) / (ms3 * 1e-3) / 1e9,
+                        "unit": UNIT, "max_abs_eig_err": float(np.max(np.abs(w3.cpu().numpy() - lam[:m]))),
+                        "two_stage_speedup": ms3 / (ms / args.steps)}
+        except Exception as ex:  # reported, not hidden
+            onestage = {"error": str(ex)}
+
+    # ---- roofline of the dominant kernel class (by device time in the timed region)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    roof = None
+    if dom in ("zgemm", "dgemm"):
+        ach = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
+        roof = {"kernel": "k_gemm<complex> (DMMA mma.sync m16n8k4 f64)" if dom == "zgemm" else "k_gemm<real>",
+                "bound": "tensor", "achieved": ach, "peak": dmma_peak, "unit": "TFLOP/s",
+                "frac": ach / dmma_peak, "traffic": None,
+                "peak_source": "FP64 tensor (DMMA m16n8k4) peak measured live by gbhe_probe_fp64_peaks; "
+                               "MEASURED_PEAKS.json has no FP64 figure",
+                "launches": pd["launches"], "ms": pd["ms"]}
+    else:
+        ach = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": dfma_peak, "unit": "TFLOP/s",
+                "frac": ach / dfma_peak, "traffic": None,
+                "peak_source": "FP64 FMA pipe measured live by gbhe_probe_fp64_peaks",
+                "launches": pd["launches"], "ms": pd["ms"]}
+    classes = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 and v["flops"] > 0 else None}
+               for k, v in prof.items() if v["launches"] > 0}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only), bounded sample
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        ns = CPU_SAMPLE_N
+        ms_ = max(1, inputs.fraction_iu(ns, args.frac))
+        As, Bs, _ = inputs.make_pair(ns, args.seed, "uniform", -10.0, 10.0)
+        c0 = time.perf_counter()
+        oracle.hegv(As, Bs, 1, ms_)
+        ct = time.perf_counter() - c0
+        cpu = {"value": nominal_flops(ns, ms_) / ct / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "oracle.hegv at n=%d, m=%d (same construction), %.1f s" % (ns, ms_, ct)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
+            "config": {"workload": "n=%d complex128 Hermitian-definite pair, Lambda~U[-10,10], seed %d, "
+                                   "lowest %d eigenpairs, nb=%d" % (n, args.seed, m, nb),
+                       "n": n, "m": m, "nb": nb, "flops_per_step": nominal_flops(n, m),
+                       "flop_convention": "(32/3)n^3 + 12 n^2 m", "l2": "inputs larger than L2 (2 x %.1f GB)"
+                       % (n * n * 16 / 1e9), "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "solve_time_s": ms / args.steps / 1e3,
+            "max_abs_eig_err": eig_err,
+            "roofline": roof,
+            "kernel_classes": classes,
+            "fp64_peaks_tflops": {"dfma": dfma_peak, "dmma": dmma_peak},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "onestage": onestage,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "gen_s": gen_s,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -149,6 +149,28 @@ int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx a
                int lda, const gbhe_cplx* B, int ldb, gbhe_cplx beta, gbhe_cplx* C, int ldc, int lower,
                void* stream);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter; benchmarks difference it around a timed region). */
+unsigned long long gbhe_launch_count(void);
+
+/* Kernel-class profiler (process-wide; for benchmarks).  While enabled, the
+ * library records a pair of CUDA events on the launching stream around each
+ * launch of the classes below and accumulates the algorithmic flop and byte
+ * counts that launch performs.  gbhe_profile_enable(1) resets and starts,
+ * gbhe_profile_enable(0) stops; gbhe_profile_read synchronises the recorded
+ * events and returns, for one class, the launch count, total flops, total
+ * bytes and total device milliseconds.  No counterpart in the paper. */
+#define GBHE_PROF_ZGEMM 0  /* complex DMMA GEMM (all level-3 steps)        */
+#define GBHE_PROF_DGEMM 1  /* real DMMA GEMM (divide-and-conquer merges)   */
+#define GBHE_PROF_PANEL 2  /* stage-1 panel QR                             */
+#define GBHE_PROF_CHASE 3  /* stage-2 bulge chasing                        */
+#define GBHE_PROF_Q2 4     /* Q2 back-transform (bulge reflectors)         */
+#define GBHE_PROF_STEDC 5  /* tridiagonal divide and conquer (whole call)  */
+#define GBHE_PROF_HEMV 6   /* one-stage Hermitian matrix-vector products   */
+#define GBHE_PROF_NCLASS 8
+int gbhe_profile_enable(int on);
+int gbhe_profile_read(int cls, unsigned long long* launches, double* flops, double* bytes, double* ms);
+
 /* Human-readable text for a return/status code. */
 const char* gbhe_status_string(int code);
 

@@ -7,6 +7,11 @@
 
 using namespace gbhe;
 
+namespace gbhe {
+static unsigned long long g_launches = 0;
+void count_launch(unsigned k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+}  // namespace gbhe
+
 namespace {
 
 int default_nb(int n) {
@@ -70,6 +75,8 @@ inline const cplx* Z_(const gbhe_cplx* p) { return reinterpret_cast<const cplx*>
 extern "C" {
 
 int gbhe_default_nb(int n) { return default_nb(n); }
+
+unsigned long long gbhe_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 int gbhe_create(gbhe_handle* handle, int device) {
   if (!handle) return -1;

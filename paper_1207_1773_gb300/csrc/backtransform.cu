@@ -122,6 +122,7 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
   if (!ar.ok() || !V) { ar.off = save; return GBHE_EWORKSPACE; }
   const size_t total = (size_t)n * m;
   k_promote<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, c.st>>>(Z, ldz, n, m, X, ldx);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   // ---- Q2
   if (n >= 2) {
@@ -129,7 +130,13 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
     const size_t smem = (size_t)(2 * nb * SLAB + 2 * nb) * sizeof(cplx);
     if (smem > 48 * 1024)
       GBHE_CUDA(cudaFuncSetAttribute(k_apply_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    double fl = 0.0;
+    if (prof_on())
+      for (int s = 0; s <= n - 2; ++s)
+        for (int a0 = s + 1; a0 < n; a0 += nb) fl += 16.0 * std::min(nb, n - a0) * (double)m;
+    ProfScope prof(c.st, GBHE_PROF_Q2, fl, 16.0 * ((double)n * J * nb + 2.0 * (double)n * m));
     k_apply_q2<<<(m + SLAB - 1) / SLAB, QT, smem, c.st>>>(n, nb, m, J, V2, tau2, X, ldx);
+    count_launch();
     GBHE_CUDA(cudaGetLastError());
   }
   // ---- Q1
@@ -139,6 +146,7 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
   for (int p = npan - 1; p >= 0; --p) {
     const int k = p * nb, mp = n - k - nb, kr = std::min(nb, mp);
     k_panel_v<<<(int)std::min<size_t>(((size_t)mp * nb + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, k, nb, mp, kr, V, n);
+    count_launch();
     GBHE_CUDA(cudaGetLastError());
     cplx* Xr = X + (k + nb);
     const cplx* T = T1 + (size_t)p * nb * nb;

@@ -107,6 +107,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
   return ok_s != 0;
 }
 
+// Host-side count of kernel launches made by this library (benchmark claim).
+void count_launch(unsigned k = 1);
+
 // Host-side bump allocator over the caller's workspace.
 struct Arena {
   char* base;

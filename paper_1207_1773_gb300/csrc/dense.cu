@@ -181,6 +181,7 @@ int potrf_run(Ctx& c, int n, cplx* B, int ldb) {
   for (int k0 = 0; k0 < n; k0 += DB) {
     const int bs = std::min(DB, n - k0);
     k_potrf_diag<<<1, DT, diag_smem(), c.st>>>(B, ldb, k0, bs, Linv, c.status);
+    count_launch();
     GBHE_CUDA(cudaGetLastError());
     const int rest = n - k0 - bs;
     if (rest <= 0) break;
@@ -206,6 +207,7 @@ int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, i
   const int nblk = (n + DB - 1) / DB;
   cplx* Linv = c.dense_scratch;
   k_trtri_diag<<<nblk, DT, diag_smem(), c.st>>>(L, ldl, n, Linv);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   if (trans == 0) {
     for (int b = 0; b < nblk; ++b) {
@@ -243,15 +245,18 @@ int hegst_run(Ctx& c, int n, cplx* A, int lda, const cplx* L, int ldl) {
   if (n <= 0) return 0;
   const size_t total = (size_t)n * n;
   k_fill_upper<<<grid1d(total), 256, 0, c.st>>>(A, lda, n);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   int rc = trsm_run(c, 0, n, n, L, ldl, A, lda);  // W = L^{-1} A
   if (rc) return rc;
   dim3 tg((n + 31) / 32, (n + 31) / 32);
   k_conj_transpose<<<tg, dim3(32, 8), 0, c.st>>>(A, lda, n);  // W^H
   GBHE_CUDA(cudaGetLastError());
+  count_launch();
   rc = trsm_run(c, 0, n, n, L, ldl, A, lda);  // L^{-1} W^H = A'^H
   if (rc) return rc;
   k_hermitize<<<grid1d(total), 256, 0, c.st>>>(A, lda, n);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   return 0;
 }

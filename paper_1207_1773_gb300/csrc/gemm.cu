@@ -8,7 +8,7 @@
 // multiplied (register double buffering).  Shared-memory rows are padded to
 // 68 doubles so that the fragment loads of a half-warp hit 16 distinct banks.
 #include <algorithm>
-#include "gemm.cuh"
+#include "internal.cuh"
 
 namespace gbhe {
 namespace {
@@ -256,9 +256,16 @@ int gemm_launch(cudaStream_t st, const GemmArgs& g, void* scratch, size_t scratc
     h.k = 0;
     dim3 grid((g.m + BM - 1) / BM, (g.n + BN - 1) / BN, 1);
     k_gemm<CPLX><<<grid, NT, 0, st>>>(h, 1, nullptr);
+    count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
   }
   const int tm = (g.m + BM - 1) / BM, tn = (g.n + BN - 1) / BN;
+  // algorithmic flops of this call (lower-only: the lower triangle of a square C)
+  const double outs = g.lower_only ? (double)g.n * (g.n + 1) / 2 + (double)(g.m - g.n) * g.n : (double)g.m * g.n;
+  const double flops = (CPLX ? 8.0 : 2.0) * outs * g.k;
+  const double esz = CPLX ? 16.0 : 8.0;
+  const double bytes = esz * ((double)g.m * g.k + (double)g.k * g.n + outs * (g.beta.x != 0.0 || g.beta.y != 0.0 ? 2 : 1));
+  ProfScope prof(st, CPLX ? GBHE_PROF_ZGEMM : GBHE_PROF_DGEMM, flops, bytes);
   int nsplit = 1;
   const long tiles = (long)tm * tn;
   if (scratch && tiles < 96 && g.k >= 1024) {
@@ -269,6 +276,7 @@ int gemm_launch(cudaStream_t st, const GemmArgs& g, void* scratch, size_t scratc
   if (nsplit <= 1) {
     dim3 grid(tm, tn, 1);
     k_gemm<CPLX><<<grid, NT, 0, st>>>(g, g.k, nullptr);
+    count_launch();
   } else {
     int kchunk = (g.k + nsplit - 1) / nsplit;
     kchunk = (kchunk + BK - 1) / BK * BK;
@@ -277,9 +285,11 @@ int gemm_launch(cudaStream_t st, const GemmArgs& g, void* scratch, size_t scratc
     GemmArgs h = g;
     h.lower_only = 0;
     k_gemm<CPLX><<<grid, NT, 0, st>>>(h, kchunk, reinterpret_cast<cplx*>(scratch));
+    count_launch();
     const size_t total = (size_t)g.m * g.n;
     int blocks = (int)std::min<size_t>((total + 255) / 256, 1024);
     k_splitk_reduce<CPLX><<<blocks, 256, 0, st>>>(g, nsplit, reinterpret_cast<const cplx*>(scratch));
+    count_launch();
   }
   return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
 }
@@ -296,7 +306,9 @@ int dgemm_grouped(cudaStream_t st, const DGroupDesc* d_desc, int ngroups, int ma
                   double alpha, double beta) {
   if (ngroups <= 0 || max_m <= 0 || max_n <= 0) return 0;
   dim3 grid((max_m + BM - 1) / BM, (max_n + BN - 1) / BN, ngroups);
+  ProfScope prof(st, GBHE_PROF_DGEMM, 0.0, 0.0);  // sizes live on the device
   k_dgemm_grouped<<<grid, NT, 0, st>>>(d_desc, alpha, beta);
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
 }
 

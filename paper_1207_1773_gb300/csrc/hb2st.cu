@@ -257,6 +257,7 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
   if (!a.ok() || !WB) { a.off = save; return GBHE_EWORKSPACE; }
   const int J = hb2st_J(n, nb);
   k_band_in<<<std::min<size_t>(((size_t)ldb * n + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, n, nb, WB, ldb);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   GBHE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * n, c.st));
   if (n >= 2) {
@@ -265,9 +266,25 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     ca.progress = prog; ca.st = c.status;
     const int G = std::min(c.num_sms, n - 1);
     void* args[] = {&ca};
+    count_launch();
+    double fl = 0.0;
+    if (prof_on()) {
+      // per step: E H (2 L Lp), H^H E (2 L (Lp-1)), two-sided (2 L^2) complex multiply-adds
+      for (int s = 0; s <= n - 2; ++s) {
+        int Lp = 0;
+        for (int a0 = s + 1; a0 < n; a0 += nb) {
+          const int L = std::min(nb, n - a0);
+          fl += 8.0 * (2.0 * L * Lp + 2.0 * L * std::max(Lp - 1, 0) + 2.0 * L * L);
+          Lp = L;
+        }
+      }
+    }
+    const double by = 16.0 * ((double)n * J * nb + 2.0 * ldb * n);
+    ProfScope prof(c.st, GBHE_PROF_CHASE, fl, by);
     GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_chase, dim3(G), dim3(HT), args, 0, c.st));
   }
   k_band_out<<<std::min((n + 255) / 256, 1024), 256, 0, c.st>>>(WB, ldb, n, d, e);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   a.off = save;
   return 0;

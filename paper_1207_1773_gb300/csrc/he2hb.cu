@@ -205,7 +205,12 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
     pa.part = part; pa.alpha = alpha; pa.bar = reinterpret_cast<unsigned*>(c.status + ST_BAR);
     pa.st = c.status;
     void* args[] = {&pa};
-    GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PT), args, smem, c.st));
+    count_launch();
+    {
+      const double fl = 4.0 * (2.0 * mp * (double)kr * kr - 2.0 * (double)kr * kr * kr / 3.0);
+      ProfScope prof(c.st, GBHE_PROF_PANEL, fl, 2.0 * 16.0 * mp * nb);
+      GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PT), args, smem, c.st));
+    }
     // ---- trailing update
     cplx* A22 = A + (size_t)(k + nb) + (size_t)(k + nb) * lda;
     const cplx* T = pa.T;

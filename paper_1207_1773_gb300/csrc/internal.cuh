@@ -19,6 +19,22 @@ struct Ctx {
 
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(32) << 20;
 
+// RAII marker for the optional profiler: records CUDA events around the
+// enclosed launches of class `cls` when profiling is on (prof.cu).
+bool prof_on();
+class ProfScope {
+ public:
+  ProfScope(cudaStream_t st, int cls, double flops, double bytes);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int cls_;
+  void* ev_;
+};
+
 size_t dense_ws_bytes(int n);
 int potrf_run(Ctx& c, int n, cplx* B, int ldb);
 int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, int ldx);

@@ -649,12 +649,16 @@ int stedc_run(Ctx& c, int n, const double* d, const double* e, int il, int iu, d
   a.st = c.status;
   if (!ar.ok() || !a.desc) { ar.off = save; return GBHE_EWORKSPACE; }
 
+  ProfScope prof(c.st, GBHE_PROF_STEDC, 0.0, 0.0);
   k_scale_tear<<<1, 1024, 0, c.st>>>(a, d, e);
+  count_launch();
   GBHE_CUDA(cudaMemsetAsync(a.Z, 0, nn * nn * sizeof(double), c.st));
   k_leaf<<<(a.nleaf + 3) / 4, 128, 0, c.st>>>(a);
+  count_launch();
   GBHE_CUDA(cudaGetLastError());
   if (a.nleaf == 1) {
     k_single_out<<<1, 256, 0, c.st>>>(a, il, iu, w, Zout, ldz);
+    count_launch();
     ar.off = save;
     return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
   }
@@ -666,17 +670,26 @@ int stedc_run(Ctx& c, int n, const double* d, const double* e, int il, int iu, d
     // largest node (rows) at this level, for the GEMM grid
     const int span = std::min(n, (1 << lev) * LS);
     k_deflate<<<nnodes, 256, 0, c.st>>>(a, lev);
+    count_launch();
     k_rotate<<<nnodes, 256, 0, c.st>>>(a, lev);
+    count_launch();
     k_gather<<<n, 128, 0, c.st>>>(a, lev);
+    count_launch();
     k_secular<<<(n + 127) / 128, 128, 0, c.st>>>(a, lev);
+    count_launch();
     k_zhat<<<(n + 127) / 128, 128, 0, c.st>>>(a, lev);
+    count_launch();
     k_qbuild<<<(n + 3) / 4, 128, 0, c.st>>>(a, lev);
+    count_launch();
     k_positions<<<nnodes, 256, 0, c.st>>>(a, lev, last, il, iu, w);
+    count_launch();
     k_descs<<<(nnodes + 127) / 128, 128, 0, c.st>>>(a, lev, nnodes, last, il, iu, Zout, ldz, cmap_last);
+    count_launch();
     GBHE_CUDA(cudaGetLastError());
     int rc = dgemm_grouped(c.st, a.desc, 2 * nnodes, span, span, 1.0, 0.0);
     if (rc) { ar.off = save; return rc; }
     k_copy_defl<<<n, 128, 0, c.st>>>(a, lev, last, il, iu, Zout, ldz);
+    count_launch();
     GBHE_CUDA(cudaGetLastError());
   }
   ar.off = save;

@@ -67,6 +67,11 @@ def _load():
             "gbhe_hegv_onestage": ([P, I, P, I, P, I, I, I, P, P, I, P], I),
             "gbhe_status_string": ([I], ctypes.c_char_p),
             "gbhe_zgemm": ([P, I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
+            "gbhe_launch_count": ([], ctypes.c_ulonglong),
+            "gbhe_profile_enable": ([I], I),
+            "gbhe_profile_read": ([I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
+            "gbhe_probe_fp64_peaks": ([I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -85,7 +90,8 @@ def exported_symbols():
                         "gbhe_get_status", "gbhe_default_nb", "gbhe_potrf", "gbhe_hegst", "gbhe_he2hb",
                         "gbhe_hb2st_sizes", "gbhe_hb2st", "gbhe_stedc", "gbhe_unmtr_2stage",
                         "gbhe_trsm_lh", "gbhe_hegv", "gbhe_hegv_onestage", "gbhe_status_string",
-                        "gbhe_zgemm")]
+                        "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
+                        "gbhe_probe_fp64_peaks")]
 
 
 def status_string(code: int) -> str:
@@ -275,6 +281,35 @@ def trsm_lh(L, X):
     n, m = X.shape
     h.ensure_workspace(n, 0, m)
     _check("gbhe_trsm_lh", _load().gbhe_trsm_lh(h.h, n, m, _ptr(L), _ld(L), _ptr(X), _ld(X), _stream(L.device)))
+
+
+PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6}
+
+
+def launch_count() -> int:
+    return int(_load().gbhe_launch_count())
+
+
+def profile_enable(on=True):
+    _check("gbhe_profile_enable", _load().gbhe_profile_enable(int(bool(on))))
+
+
+def profile_read():
+    """Per kernel class: dict(launches, flops, bytes, ms)."""
+    out = {}
+    for name, cls in PROF_CLASSES.items():
+        L, F, B, M = ctypes.c_ulonglong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check("gbhe_profile_read", _load().gbhe_profile_read(cls, ctypes.byref(L), ctypes.byref(F),
+                                                              ctypes.byref(B), ctypes.byref(M)))
+        out[name] = {"launches": int(L.value), "flops": F.value, "bytes": B.value, "ms": M.value}
+    return out
+
+
+def probe_fp64_peaks(device=0):
+    """Live FP64 peaks (TFLOP/s): (DFMA pipe, DMMA m16n8k4 tensor pipe)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check("gbhe_probe_fp64_peaks", _load().gbhe_probe_fp64_peaks(int(device), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 OPS = {"N": 0, "T": 1, "C": 2, "H": 3}

@@ -207,7 +207,8 @@ def test_stedc_deflation_cases(G):
     # diagonal matrix: everything deflates
     d2 = rng.standard_normal(200)
     w2, Z2 = G.stedc(torch.tensor(d2, device=DEV), torch.zeros(199, dtype=torch.float64, device=DEV))
-    assert np.array_equal(_np(w2), np.sort(d2))
+    # exact up to the two roundings of the internal scaling by max |T|
+    assert np.all(np.abs(_np(w2) - np.sort(d2)) <= 4 * EPS * np.abs(d2).max())
 
 
 @pytest.mark.parametrize("il,iu", [(1, 40), (100, 180), (250, 300)])
