@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-onestage", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--micro", default=None, help="e.g. zgemm:4096:4096:64:N:C:1 (profiling aid)")
     return p.parse_args()
 
 
@@ -350,8 +351,46 @@ def run_ours(args):
     return 0
 
 
+def run_micro(spec):
+    """Micro-benchmark of one library kernel (for profiling), e.g.
+    zgemm:M:N:K:opA:opB:lower  -- times 5 calls after 2 warm-ups."""
+    import torch
+
+    from paper_1207_1773_gb300 import gbhegv as G
+    parts = spec.split(":")
+    dev = torch.device("cuda", 0)
+    if parts[0] != "zgemm":
+        raise ValueError(spec)
+    M, N, K = int(parts[1]), int(parts[2]), int(parts[3])
+    opA, opB, lower = parts[4], parts[5], int(parts[6])
+    g = torch.Generator(device=dev).manual_seed(0)
+    ra, ca = (M, K) if opA in ("N", "H") else (K, M)
+    rb, cb = (K, N) if opB == "N" else (N, K)
+    A = torch.randn((ca, ra), dtype=torch.complex128, device=dev, generator=g).t()
+    B = torch.randn((cb, rb), dtype=torch.complex128, device=dev, generator=g).t()
+    C = torch.randn((N, M), dtype=torch.complex128, device=dev, generator=g).t()
+    for _ in range(2):
+        G.zgemm(opA, opB, A, B, C, -1.0, 1.0, lower=bool(lower))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        G.zgemm(opA, opB, A, B, C, -1.0, 1.0, lower=bool(lower))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    outs = (N * (N + 1) / 2 + (M - N) * N) if lower else M * N
+    fl = 8.0 * outs * K
+    _, dmma = G.probe_fp64_peaks(0)
+    print(json.dumps({"micro": spec, "ms": ms, "tflops": fl / ms / 1e9, "dmma_peak_tflops": dmma,
+                      "frac": fl / ms / 1e9 / dmma}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.micro:
+        return run_micro(args.micro)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
