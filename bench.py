@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "generalized solve time (s) & GFLOP/s at n=10k complex128 vs one-stage on same GPU"
 UNIT = "GFLOP/s"
-CPU_SAMPLE_N = 1536
+CPU_SAMPLE_N = 2048
 
 
 def nominal_flops(n, m):
@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-onestage", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--micro", default=None, help="e.g. zgemm:4096:4096:64:N:C:1 (profiling aid)")
+    p.add_argument("--cache", default=None, help="directory to keep the generated input pair between runs")
     return p.parse_args()
 
 
@@ -178,8 +179,18 @@ def run_ours(args):
     m = max(1, inputs.fraction_iu(n, args.frac))
     nb = args.nb
     t0 = time.time()
-    A_np, B_np, lam = inputs.make_pair(n, args.seed + rank, "uniform", -10.0, 10.0,
-                                       device=dev if n > 3000 else None)
+    cache = None
+    if args.cache:
+        cache = os.path.join(args.cache, "pair_n%d_seed%d.npz" % (n, args.seed + rank))
+    if cache and os.path.exists(cache):
+        z = np.load(cache)
+        A_np, B_np, lam = z["A"], z["B"], z["lam"]
+    else:
+        A_np, B_np, lam = inputs.make_pair(n, args.seed + rank, "uniform", -10.0, 10.0,
+                                           device=dev if n > 3000 else None)
+        if cache:
+            os.makedirs(args.cache, exist_ok=True)
+            np.savez(cache, A=A_np, B=B_np, lam=lam)
     gen_s = time.time() - t0
     A0 = G.colmajor(A_np, dev)
     B0 = G.colmajor(B_np, dev)
