@@ -137,12 +137,13 @@ __global__ void __launch_bounds__(128) k_hemv(const cplx* A22, int lda, int L, c
     atomicAdd(&y[r0 + tid].x, s.x);
     atomicAdd(&y[r0 + tid].y, s.y);
   }
-  if (bi == bj) return;
   __syncthreads();
-  // columns: y[c0+c] += sum_r conj(T[r][c]) vr[r]
+  // columns (the mirrored upper triangle): y[c0+c] += sum_r conj(T[r][c]) vr[r],
+  // over the strictly lower elements only in a diagonal tile
   const int c = tid & 31;
   acc = mk(0.0, 0.0);
-  for (int rr = qt * 8; rr < qt * 8 + 8; ++rr) ccfma(acc, T[rr][c], vr[rr]);
+  for (int rr = qt * 8; rr < qt * 8 + 8; ++rr)
+    if (bi != bj || rr > c) ccfma(acc, T[rr][c], vr[rr]);
   part[qt][c] = acc;
   __syncthreads();
   if (tid < HT && c0 + tid < L) {

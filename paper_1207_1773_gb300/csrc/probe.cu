@@ -18,9 +18,13 @@ __global__ void k_probe_dfma(double* out, double s) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// The operands change every iteration and the accumulators start distinct:
+// with loop-invariant operands the measured rate comes out twice the real one.
 __global__ void k_probe_dmma(double* out) {
-  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, b = 1.0 + threadIdx.x * 1e-4;
-  double c[4][4] = {};
+  double a0 = threadIdx.x * 1e-3 + blockIdx.x, a1 = a0 + 1, b = 1.0 + threadIdx.x * 1e-4;
+  double c[4][4];
+  for (int j = 0; j < 4; ++j)
+    for (int q = 0; q < 4; ++q) c[j][q] = 0.5 * j + q;
   for (int i = 0; i < ITERS; ++i) {
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -29,6 +33,7 @@ __global__ void k_probe_dmma(double* out) {
           "{%0,%1,%2,%3};"
           : "+d"(c[j][0]), "+d"(c[j][1]), "+d"(c[j][2]), "+d"(c[j][3])
           : "d"(a0), "d"(a1), "d"(b));
+    a0 += 1e-9;
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = c[0][0] + c[1][1] + c[2][2] + c[3][3];
 }

@@ -287,6 +287,21 @@ def test_hegv_fraction(G, frac):
     _cluster_subspace_check(A, B, w, X, wo, Xo)
 
 
+@pytest.mark.parametrize("n,il,iu", [(1, 1, 1), (2, 1, 2), (33, 1, 33), (100, 1, 100), (130, 1, 13), (257, 20, 90)])
+def test_hegv_onestage(G, n, il, iu):
+    A, B, lam = inputs.make_pair(n, 11)
+    w, X = G.hegv(_c(A), _c(B), il, iu, onestage=True)
+    w, X = _np(w), _np(X)
+    wo, Xo, info = oracle.hegv(A, B, il, iu)
+    m = iu - il + 1
+    tol = 10 * n * EPS * np.linalg.norm(A, 2) / np.linalg.eigvalsh(B).min()
+    assert np.max(np.abs(w - wo)) <= tol
+    res = np.linalg.norm(A @ X - (B @ X) * w[None, :]) / (n * EPS * np.linalg.norm(A) * np.linalg.norm(X))
+    orth = np.linalg.norm(X.conj().T @ B @ X - np.eye(m)) / (n * EPS)
+    assert res <= 100 and orth <= 100, (res, orth)
+    _cluster_subspace_check(A, B, w, X, wo, Xo)
+
+
 def test_hegv_clustered_illconditioned(G):
     n = 320
     A, B, lam = inputs.make_pair(n, 2, "clustered", -1, 1, ldiag="loguniform")
