@@ -68,6 +68,17 @@ int gbhe_get_status(gbhe_handle handle, void* stream);
 /* Default band width used when nb = 0 is passed. */
 int gbhe_default_nb(int n);
 
+/* Engine of the FP64 level-3 products of every stage:
+ *   GBHE_ENGINE_CRT  (default) exact modular products on the FP16 tensor
+ *                    cores for large products (see gbhe_gemm_crt), the FP64
+ *                    tensor pipe (DMMA) for small ones;
+ *   GBHE_ENGINE_DMMA FP64 tensor pipe only.
+ * The paper's level-3 BLAS on the GPU (Section 3) has one engine; the choice
+ * exists because this GPU's FP64 pipes are about 1 TFLOP/s. */
+#define GBHE_ENGINE_DMMA 0
+#define GBHE_ENGINE_CRT 1
+int gbhe_set_gemm_engine(gbhe_handle h, int engine);
+
 /* Algorithm 1, step 1 (paper Section 3): Cholesky factorisation B = L L^H.
  * B (n x n, ldb) lower triangle read; L overwrites it (upper untouched).
  * A non-positive pivot at order k sets status k (first failure wins). */
@@ -149,6 +160,19 @@ int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx a
                int lda, const gbhe_cplx* B, int ldb, gbhe_cplx beta, gbhe_cplx* C, int ldc, int lower,
                void* stream);
 
+/* The same product computed on the FP16 tensor cores with exact modular
+ * arithmetic (16 moduli <= 256, Chinese remainder reconstruction, one final
+ * rounding to double): as accurate as an FP64 GEMM for operands whose
+ * rows/columns are not strongly graded.  Complex (cplx != 0, gbhe_cplx
+ * operands) or real (cplx = 0, double operands).  opA in {0,1,2,3} as for
+ * gbhe_zgemm, opB in {0,1,2}; k <= 65536.  Needs gbhe_crt_workspace_size bytes
+ * of workspace beyond the common part (see gbhe_workspace_size); returns
+ * GBHE_EWORKSPACE otherwise.  No counterpart in the paper (a GB300-specific
+ * way of doing its level-3 products). */
+int gbhe_crt_workspace_size(int m, int n, int k, int cplx, size_t* bytes);
+int gbhe_gemm_crt(gbhe_handle h, int cplx, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const void* A,
+                  int lda, const void* B, int ldb, gbhe_cplx beta, void* C, int ldc, int lower, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (host-side counter; benchmarks difference it around a timed region). */
 unsigned long long gbhe_launch_count(void);
@@ -167,6 +191,7 @@ unsigned long long gbhe_launch_count(void);
 #define GBHE_PROF_Q2 4     /* Q2 back-transform (bulge reflectors)         */
 #define GBHE_PROF_STEDC 5  /* tridiagonal divide and conquer (whole call)  */
 #define GBHE_PROF_HEMV 6   /* one-stage Hermitian matrix-vector products   */
+#define GBHE_PROF_CRT 7    /* FP64-exact GEMM on FP16 tensor cores (CRT)   */
 #define GBHE_PROF_NCLASS 8
 int gbhe_profile_enable(int on);
 int gbhe_profile_read(int cls, unsigned long long* launches, double* flops, double* bytes, double* ms);

@@ -22,7 +22,7 @@ int default_nb(int n) {
 
 // Workspace every call carves first: split-K scratch and the diagonal-block
 // inverses.
-size_t common_bytes(int n) { return GEMM_SCRATCH_BYTES + dense_ws_bytes(n) + 512; }
+size_t common_bytes(int n) { return GEMM_SCRATCH_BYTES + dense_ws_bytes(n) + crt_budget_bytes(n) + 1024; }
 
 size_t stage_bytes(gbhe_handle h, int n, int nb, int m) {
   size_t s = 0;
@@ -63,6 +63,20 @@ int make_ctx(gbhe_handle h, int n, void* stream, Ctx* c) {
   c->gemm_scratch_bytes = GEMM_SCRATCH_BYTES;
   c->dense_scratch = c->arena.take<cplx>(dense_ws_bytes(n) / sizeof(cplx));
   if (!c->arena.ok() || !c->gemm_scratch) return GBHE_EWORKSPACE;
+  c->engine = h->engine;
+  c->crt_ws = nullptr;
+  c->crt_ws_bytes = 0;
+  if (h->engine == GBHE_ENGINE_CRT) {
+    const size_t cb = crt_budget_bytes(n);
+    const size_t save = c->arena.off;
+    char* ws = c->arena.take<char>(cb);
+    if (c->arena.ok() && ws) {
+      c->crt_ws = ws;
+      c->crt_ws_bytes = cb;
+    } else {
+      c->arena.off = save;  // workspace too small for the tensor-core engine: DMMA only
+    }
+  }
   if (cudaSetDevice(h->device) != cudaSuccess) return GBHE_ECUDA;
   return 0;
 }
@@ -75,6 +89,13 @@ inline const cplx* Z_(const gbhe_cplx* p) { return reinterpret_cast<const cplx*>
 extern "C" {
 
 int gbhe_default_nb(int n) { return default_nb(n); }
+
+int gbhe_set_gemm_engine(gbhe_handle h, int engine) {
+  if (!h) return -1;
+  if (engine != GBHE_ENGINE_DMMA && engine != GBHE_ENGINE_CRT) return -2;
+  h->engine = engine;
+  return 0;
+}
 
 unsigned long long gbhe_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
@@ -96,6 +117,7 @@ int gbhe_create(gbhe_handle* handle, int device) {
   h->work = nullptr;
   h->work_bytes = 0;
   h->spin_limit = 0;
+  h->engine = GBHE_ENGINE_CRT;
   *handle = h;
   return 0;
 }
@@ -360,6 +382,45 @@ int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx a
   return zgemm(c.st, gemm_args(opA, opB, m, n, k, mk(alpha.re, alpha.im), A, lda, B, ldb, mk(beta.re, beta.im), C,
                                ldc, lower),
                c.gemm_scratch, c.gemm_scratch_bytes);
+}
+
+int gbhe_crt_workspace_size(int m, int n, int k, int cplx, size_t* bytes) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (k < 0 || k > 65536) return -3;
+  if (!bytes) return -5;
+  *bytes = crt_gemm_ws_bytes(std::max(m, 1), std::max(n, 1), std::max(k, 1), cplx ? 1 : 0);
+  return 0;
+}
+
+int gbhe_gemm_crt(gbhe_handle h, int cplx, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const void* A,
+                  int lda, const void* B, int ldb, gbhe_cplx beta, void* C, int ldc, int lower, void* stream) {
+  if (!h) return -1;
+  if (opA < 0 || opA > 3 || (!cplx && opA == OP_H)) return -3;
+  if (opB < 0 || opB > 2) return -4;
+  if (m < 0) return -5;
+  if (n < 0) return -6;
+  if (k < 0 || k > 65536) return -7;
+  const int ra = (opA == OP_N || opA == OP_H) ? m : k;
+  if (m > 0 && k > 0 && !A) return -9;
+  if (lda < std::max(1, ra)) return -10;
+  const int rb = (opB == OP_N) ? k : n;
+  if (n > 0 && k > 0 && !B) return -11;
+  if (ldb < std::max(1, rb)) return -12;
+  if (m > 0 && n > 0 && !C) return -14;
+  if (ldc < std::max(1, m)) return -15;
+  if (opA == OP_H && m != k) return -3;
+  Ctx c;
+  int rc = make_ctx(h, 1, stream, &c);
+  if (rc) return rc;
+  if (m == 0 || n == 0) return 0;
+  GemmArgs g = gemm_args(opA, opB, m, n, k, mk(alpha.re, alpha.im), A, lda, B, ldb, mk(beta.re, beta.im), C, ldc,
+                         lower);
+  if (k == 0) return cplx ? zgemm(c.st, g, nullptr, 0) : dgemm(c.st, g, nullptr, 0);
+  const size_t need = crt_gemm_ws_bytes(m, n, k, cplx ? 1 : 0);
+  char* ws = c.arena.take<char>(need);
+  if (!c.arena.ok() || !ws) return GBHE_EWORKSPACE;
+  return crt_gemm(c.st, g, cplx ? 1 : 0, ws, need);
 }
 
 }  // extern "C"

@@ -151,12 +151,12 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
     cplx* Xr = X + (k + nb);
     const cplx* T = T1 + (size_t)p * nb * nb;
     int rc;
-    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, kr, m, mp, one, V, n, Xr, ldx, zero, W1, nb), c.gemm_scratch,
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, kr, m, mp, one, V, n, Xr, ldx, zero, W1, nb), c.gemm_scratch,
                     c.gemm_scratch_bytes))) { ar.off = save; return rc; }
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, kr, m, kr, one, T, nb, W1, nb, zero, W2, nb), nullptr, 0))) {
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, kr, m, kr, one, T, nb, W1, nb, zero, W2, nb), nullptr, 0))) {
       ar.off = save; return rc;
     }
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, mp, m, kr, mone, V, n, W2, nb, one, Xr, ldx), nullptr, 0))) {
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, m, kr, mone, V, n, W2, nb, one, Xr, ldx), nullptr, 0))) {
       ar.off = save; return rc;
     }
   }

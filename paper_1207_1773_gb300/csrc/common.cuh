@@ -140,6 +140,7 @@ struct gbhe_ctx {
   void* work;           // caller-owned device workspace
   size_t work_bytes;
   unsigned spin_limit;  // test hook (0 = default)
+  int engine;           // GBHE_ENGINE_CRT (default) or GBHE_ENGINE_DMMA
 };
 
 #define GBHE_CUDA(call)                                      \

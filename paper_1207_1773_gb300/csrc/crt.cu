@@ -1,0 +1,680 @@
+// crt.cu -- FP64-accurate GEMM on the FP16 tensor cores by exact modular
+// arithmetic (a GB300-specific replacement for FP64 level-3 products: this
+// GPU's FP64 pipes, scalar and tensor alike, deliver about 1 TFLOP/s while
+// its FP16 tensor cores deliver hundreds).
+//
+//   1. Scaling.  Every row i of op(A) is scaled by 2^(52 - ea_i) and every
+//      column j of op(B) by 2^(52 - eb_j), ea/eb the smallest exponents with
+//      |x| < 2^e over the row/column, and rounded to integers |v| <= 2^52
+//      (integer bit manipulation, exact apart from that rounding, which is at
+//      the level of the last bit of the largest element of the row/column).
+//   2. Residues.  The integers are reduced modulo NMOD = 16 pairwise coprime
+//      moduli p_l <= 256 (product M ~ 2^125) to symmetric residues |r| <= 128,
+//      exact in FP16.  Complex operands give three planes per modulus:
+//      Re, Im and Re + Im (Karatsuba, exact in modular arithmetic).
+//   3. Products.  For each modulus the three residue products
+//      P1 = Ar Br, P2 = Ai Bi, P3 = (Ar + Ai)(Br + Bi) run on mma.sync
+//      m16n8k16 f16 -> f32.  Every partial sum of at most KC = 512 products
+//      of |r| <= 128 stays below 2^23, so the FP32 accumulation is exact;
+//      after each chunk the sums are reduced mod p_l.  Re C = P1 - P2,
+//      Im C = P3 - P1 - P2 (mod p_l) are stored as bytes.
+//   4. Reconstruction.  C_int = sum_l c_l W_l - q M (CRT, W_l = M_l (M_l^-1
+//      mod p_l)) in 160-bit integer arithmetic, q = round(sum_l c_l y_l/p_l)
+//      (the true value is far inside (-M/2, M/2): |C_int| <= K 2^105 < M/8
+//      for K <= 2^16, and the FP32 estimate of q errs by less than 2^-8),
+//      then converted to the nearest double and scaled by
+//      2^(ea_i + eb_j - 104) -- all with integer instructions.
+// The result equals the exact product of the rounded operands, rounded once
+// to double: as accurate as an FP64 GEMM for operands whose rows/columns are
+// not strongly graded.
+#include <algorithm>
+#include <cstring>
+#include <cuda_fp16.h>
+#include "internal.cuh"
+
+namespace gbhe {
+namespace {
+
+constexpr int NMOD = 16;
+constexpr int KC = 512;              // exact FP32 chunk length
+constexpr int CBM = 128, CBN = 64, CBK = 32, CNT = 256, CSTAGE = 3;
+constexpr int KPAD = CBK + 8;        // smem row pitch in halfs (80 B: ldmatrix conflict-free)
+constexpr int KMAX = 65536;          // contraction bound of the margin argument above
+
+const int h_mod[NMOD] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 211, 199, 197, 193, 191};
+
+__constant__ int c_p[NMOD];
+__constant__ float c_pinv[NMOD];
+__constant__ float c_frac[NMOD];         // y_l / p_l
+__constant__ unsigned c_W[NMOD][4];      // W_l (128-bit, little-endian words)
+__constant__ unsigned c_M[4];            // M
+__constant__ int c_k18[NMOD], c_k36[NMOD];  // 2^18 mod p, 2^36 mod p
+
+bool g_const_ready = false;
+
+int init_constants() {
+  if (g_const_ready) return 0;
+  typedef unsigned __int128 u128;
+  u128 M = 1;
+  for (int l = 0; l < NMOD; ++l) M *= (u128)h_mod[l];
+  int p[NMOD], k18[NMOD], k36[NMOD];
+  float pinv[NMOD], frac[NMOD];
+  unsigned W[NMOD][4], Mw[4];
+  for (int l = 0; l < NMOD; ++l) {
+    const int pl = h_mod[l];
+    const u128 Ml = M / (u128)pl;
+    const int mr = (int)(Ml % (u128)pl);
+    int y = 0;
+    for (int t = 1; t < pl; ++t)
+      if ((mr * t) % pl == 1) { y = t; break; }
+    const u128 Wl = (Ml * (u128)y) % M;
+    for (int w = 0; w < 4; ++w) W[l][w] = (unsigned)(Wl >> (32 * w));
+    p[l] = pl;
+    pinv[l] = 1.0f / (float)pl;
+    frac[l] = (float)((double)y / (double)pl);
+    k18[l] = (int)(((u128)1 << 18) % (u128)pl);
+    k36[l] = (int)(((u128)1 << 36) % (u128)pl);
+  }
+  for (int w = 0; w < 4; ++w) Mw[w] = (unsigned)(M >> (32 * w));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_p, p, sizeof(p)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_pinv, pinv, sizeof(pinv)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_frac, frac, sizeof(frac)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_W, W, sizeof(W)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_M, Mw, sizeof(Mw)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_k18, k18, sizeof(k18)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_k36, k36, sizeof(k36)));
+  g_const_ready = true;
+  return 0;
+}
+
+// ------------------------------------------------------------------ operand access
+// Element (r, k) of the operand: for op(A) r is the row, for op(B) r is the
+// column of op(B); k runs along the contraction.  `mode` encodes the storage:
+//   0: X[r + k ld]            (A with N;  B with T or C)
+//   1: X[k + r ld]            (A with T or C;  B with N)
+//   2: Hermitian, lower stored: r >= k ? X[r + k ld] : conj X[k + r ld]
+// `cj` conjugates every element (A with C, B with C).
+struct Operand {
+  const void* X;
+  int ld, R, K, mode, cj, cplx;
+};
+
+__device__ __forceinline__ double2 op_elem(const Operand& o, int r, int k) {
+  double2 v;
+  if (o.cplx) {
+    const double2* X = reinterpret_cast<const double2*>(o.X);
+    if (o.mode == 0) v = X[(size_t)r + (size_t)k * o.ld];
+    else if (o.mode == 1) v = X[(size_t)k + (size_t)r * o.ld];
+    else if (r >= k) { v = X[(size_t)r + (size_t)k * o.ld]; if (r == k) v.y = 0.0; }
+    else { v = X[(size_t)k + (size_t)r * o.ld]; v.y = -v.y; }
+    if (o.cj) v.y = -v.y;
+  } else {
+    const double* X = reinterpret_cast<const double*>(o.X);
+    v.x = (o.mode == 0) ? X[(size_t)r + (size_t)k * o.ld] : X[(size_t)k + (size_t)r * o.ld];
+    v.y = 0.0;
+  }
+  return v;
+}
+
+__device__ __forceinline__ int exp_bound(double x) {
+  // smallest e with |x| < 2^e for normal x; zero/denormal -> -1100
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  return E == 0 ? -1100 : E - 1022;
+}
+
+// Max exponent per r over k.  Tile 32 (r) x 32 (k) per block of 32 x 8
+// threads; the contiguous storage direction maps to threadIdx.x.
+__global__ void k_op_exponents(Operand o, int* e) {
+  __shared__ int tile[32][33];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool r_contig = (o.mode == 0) || (o.mode == 2 && r0 >= k0 + 31);
+  for (int q = ty; q < 32; q += 8) {
+    const int r = r_contig ? r0 + tx : r0 + q;
+    const int k = r_contig ? k0 + q : k0 + tx;
+    int ev = -1100;
+    if (r < o.R && k < o.K) {
+      const double2 v = op_elem(o, r, k);
+      ev = max(exp_bound(v.x), exp_bound(v.y));
+    }
+    if (r_contig) tile[tx][q] = ev; else tile[q][tx] = ev;
+  }
+  __syncthreads();
+  if (ty == 0 && r0 + tx < o.R) {
+    int m = -1100;
+    for (int q = 0; q < 32; ++q) m = max(m, tile[tx][q]);
+    atomicMax(&e[r0 + tx], m);
+  }
+}
+
+__global__ void k_fill_int(int* p, int n, int v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// residue of a non-negative integer x < 2^18 modulo p (fp32 exact arithmetic)
+__device__ __forceinline__ float fmod_small(float x, float p, float pinv) {
+  float q = floorf(x * pinv);
+  float r = fmaf(-q, p, x);
+  if (r < 0.f) r += p;
+  if (r >= p) r -= p;
+  return r;
+}
+
+// Residue planes: P[(l * ncomp + c) * R * Kp + r * Kp + k] (fp16), symmetric
+// residues of the scaled integer of element (r, k); zero for k >= K.
+__global__ void k_op_residues(Operand o, const int* e, int Kp, __half* P) {
+  __shared__ double2 tile[32][33];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool r_contig = (o.mode == 0) || (o.mode == 2 && r0 >= k0 + 31);
+  for (int q = ty; q < 32; q += 8) {
+    const int r = r_contig ? r0 + tx : r0 + q;
+    const int k = r_contig ? k0 + q : k0 + tx;
+    double2 v = make_double2(0.0, 0.0);
+    if (r < o.R && k < o.K) v = op_elem(o, r, k);
+    if (r_contig) tile[tx][q] = v; else tile[q][tx] = v;
+  }
+  __syncthreads();
+  const int ncomp = o.cplx ? 3 : 1;
+  const size_t plane = (size_t)o.R * Kp;
+  for (int q = ty; q < 32; q += 8) {
+    const int r = r0 + q, k = k0 + tx;  // k contiguous in the output
+    if (r >= o.R || k >= Kp) continue;
+    const double2 v = tile[q][tx];
+    const int er = e[r];
+    // scaled integers (|v| <= 2^52) as sign + three 18-bit limbs
+    int sg[2], a[2], b[2], c[2];
+    for (int part = 0; part < 2; ++part) {
+      const double x = part ? v.y : v.x;
+      const long long bits = __double_as_longlong(x);
+      const int E = (int)((bits >> 52) & 0x7FF);
+      unsigned long long mag = 0;
+      if (E != 0 && k < o.K) {
+        const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = er - (E - 1023);  // right shift (>= 1)
+        if (sh <= 60) mag = (mant + (1ull << (sh - 1))) >> sh;
+      }
+      sg[part] = (bits < 0) ? 1 : 0;
+      a[part] = (int)(mag >> 36);
+      b[part] = (int)((mag >> 18) & 0x3FFFF);
+      c[part] = (int)(mag & 0x3FFFF);
+    }
+    for (int l = 0; l < NMOD; ++l) {
+      const float p = (float)c_p[l], pinv = c_pinv[l];
+      float rr[2];
+      for (int part = 0; part < 2; ++part) {
+        const float ra = fmod_small((float)a[part], p, pinv);
+        const float rb = fmod_small((float)b[part], p, pinv);
+        const float rc = fmod_small((float)c[part], p, pinv);
+        float t = fmaf(ra, (float)c_k36[l], fmaf(rb, (float)c_k18[l], rc));  // < 2^17
+        t = fmod_small(t, p, pinv);
+        if (sg[part] && t != 0.f) t = p - t;
+        rr[part] = t;  // in [0, p)
+      }
+      const float half_p = 0.5f * p;
+      float s0 = rr[0] > half_p ? rr[0] - p : rr[0];
+      __half* dst = P + (size_t)(l * ncomp) * plane + (size_t)r * Kp + k;
+      dst[0] = __float2half_rn(s0);
+      if (o.cplx) {
+        float s1 = rr[1] > half_p ? rr[1] - p : rr[1];
+        float ss = rr[0] + rr[1];
+        if (ss >= p) ss -= p;
+        ss = ss > half_p ? ss - p : ss;
+        dst[plane] = __float2half_rn(s1);
+        dst[2 * plane] = __float2half_rn(ss);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ residue products
+__device__ __forceinline__ void cp16(void* smem, const void* g, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(g), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+
+__device__ __forceinline__ void hmma(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float fmod_acc(float x, float p, float pinv) {
+  // x an integer-valued float with |x| <= 2^24; result in [0, p)
+  float q = floorf(x * pinv);
+  float r = fmaf(-q, p, x);
+  if (r < 0.f) r += p;
+  if (r >= p) r -= p;
+  return r;
+}
+
+// grid (ceil(M/CBM), ceil(N/CBN), NMOD); 8 warps as 4 (M) x 2 (N), warp tile 32 x 32.
+// PA: residue planes of op(A) (R = M), PB: of op(B) (R = N); both K-padded to Kp.
+// Out: bytes [l][comp][j][i] (column-major per plane), comp = re (and im).
+template <bool CPLX>
+__global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __half* PB, int M, int N, int Kp,
+                                                   unsigned char* Out) {
+  constexpr int NC = CPLX ? 3 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __half* sm = reinterpret_cast<__half*>(smem_raw);
+  constexpr int A_ST = NC * CBM * KPAD, B_ST = NC * CBN * KPAD, ST = A_ST + B_ST;
+  const int l = blockIdx.z;
+  const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int wm = (w & 3) * 32, wn = (w >> 2) * 32;
+  const float p = (float)c_p[l], pinv = c_pinv[l];
+  const size_t planeA = (size_t)M * Kp, planeB = (size_t)N * Kp;
+  const __half* Al = PA + (size_t)l * NC * planeA;
+  const __half* Bl = PB + (size_t)l * NC * planeB;
+
+  float acc[NC][2][4][4];
+  float res[CPLX ? 2 : 1][2][4][4];
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[c][a][b][q] = 0.f;
+#pragma unroll
+  for (int c = 0; c < (CPLX ? 2 : 1); ++c)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) res[c][a][b][q] = 0.f;
+
+  auto load = [&](int stage, int k0) {
+    __half* As = sm + stage * ST;
+    __half* Bs = As + A_ST;
+    // A: NC * 128 rows * 4 chunks of 16 B
+    for (int i = t; i < NC * CBM * 4; i += CNT) {
+      const int c = i / (CBM * 4), rem = i % (CBM * 4), r = rem >> 2, ch = rem & 3;
+      const bool ok = (m0 + r) < M;
+      const __half* src = Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + ch * 8;
+      cp16(As + (c * CBM + r) * KPAD + ch * 8, src, ok);
+    }
+    for (int i = t; i < NC * CBN * 4; i += CNT) {
+      const int c = i / (CBN * 4), rem = i % (CBN * 4), r = rem >> 2, ch = rem & 3;
+      const bool ok = (n0 + r) < N;
+      const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + ch * 8;
+      cp16(Bs + (c * CBN + r) * KPAD + ch * 8, src, ok);
+    }
+  };
+
+  auto flush = [&]() {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (CPLX) {
+            const float p1 = acc[0][a][b][q], p2 = acc[1][a][b][q], p3 = acc[2][a][b][q];
+            // |p| <= 2^23: differences stay exact in fp32
+            float cr = fmod_acc(p1 - p2, p, pinv);
+            float ci = fmod_acc(fmod_acc(p3, p, pinv) - fmod_acc(p1 + p2, p, pinv), p, pinv);
+            float sr = res[0][a][b][q] + cr;
+            float si = res[CPLX ? 1 : 0][a][b][q] + ci;
+            if (sr >= p) sr -= p;
+            if (si >= p) si -= p;
+            res[0][a][b][q] = sr;
+            res[CPLX ? 1 : 0][a][b][q] = si;
+          } else {
+            float s = res[0][a][b][q] + fmod_acc(acc[0][a][b][q], p, pinv);
+            if (s >= p) s -= p;
+            res[0][a][b][q] = s;
+          }
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c][a][b][q] = 0.f;
+        }
+  };
+
+  const int ktiles = Kp / CBK;
+#pragma unroll
+  for (int s = 0; s < CSTAGE - 1; ++s) {
+    if (s < ktiles) load(s, s * CBK);
+    cp_commit();
+  }
+  const int gq = lane >> 2, tq = lane & 3;
+  for (int kt = 0; kt < ktiles; ++kt) {
+    cp_wait<CSTAGE - 2>();
+    __syncthreads();
+    {
+      const int ks = kt + CSTAGE - 1;
+      if (ks < ktiles) load(ks % CSTAGE, ks * CBK);
+      cp_commit();
+    }
+    const __half* As = sm + (kt % CSTAGE) * ST;
+    const __half* Bs = As + A_ST;
+#pragma unroll
+    for (int kk = 0; kk < CBK; kk += 16) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        unsigned af[2][4], bf[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          // ldmatrix.x4 of the 16x16 A tile: lanes 0-15 rows 0-15 (k 0-7), lanes 16-31 rows 0-15 (k 8-15)
+          const int row = wm + mt * 16 + (lane & 15);
+          const int col = kk + ((lane >> 4) << 3);
+          ldsm_x4(af[mt], As + (c * CBM + row) * KPAD + col);
+        }
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          // two n8 tiles: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+          const int nrow = wn + np * 16 + (lane & 7) + ((lane >> 4) << 3);
+          const int col = kk + (((lane >> 3) & 1) << 3);
+          ldsm_x4(bf[np], Bs + (c * CBN + nrow) * KPAD + col);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+            hmma(acc[c][mt][nt], af[mt], bf[nt >> 1][(nt & 1) * 2], bf[nt >> 1][(nt & 1) * 2 + 1]);
+      }
+    }
+    if (((kt + 1) * CBK) % KC == 0) flush();
+  }
+  cp_wait<0>();
+  if ((ktiles * CBK) % KC != 0) flush();
+  (void)gq; (void)tq;
+  // store residues: element (row, col) of the 16x8 C fragment q: row = g + 8*(q>>1), col = 2*tq + (q&1)
+  const int ncout = CPLX ? 2 : 1;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = m0 + wm + a * 16 + (lane >> 2) + 8 * (q >> 1);
+        const int j = n0 + wn + b * 8 + 2 * (lane & 3) + (q & 1);
+        if (i >= M || j >= N) continue;
+        for (int c = 0; c < ncout; ++c)
+          Out[((size_t)(l * ncout + c) * N + j) * M + i] = (unsigned char)res[c][a][b][q];
+      }
+}
+
+// ------------------------------------------------------------------ reconstruction
+// 160-bit accumulate: S += c * W (c < 2^8, W 128-bit)
+__device__ __forceinline__ void mac160(unsigned (&S)[5], unsigned c, const unsigned (&W)[4]) {
+  asm("mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
+      "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
+      "madc.lo.cc.u32 %2, %5, %8, %2;\n\t"
+      "madc.lo.cc.u32 %3, %5, %9, %3;\n\t"
+      "addc.u32 %4, %4, 0;\n\t"
+      "mad.hi.cc.u32 %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %7, %2;\n\t"
+      "madc.hi.cc.u32 %3, %5, %8, %3;\n\t"
+      "madc.hi.u32 %4, %5, %9, %4;"
+      : "+r"(S[0]), "+r"(S[1]), "+r"(S[2]), "+r"(S[3]), "+r"(S[4])
+      : "r"(c), "r"(W[0]), "r"(W[1]), "r"(W[2]), "r"(W[3]));
+}
+
+// value of the 160-bit two's complement integer D times 2^sc, rounded to double
+__device__ __forceinline__ double int160_to_double(unsigned (&D)[5], int sc) {
+  const bool negv = (int)D[4] < 0;
+  if (negv) {  // D = -D
+    unsigned c = 1;
+    for (int i = 0; i < 5; ++i) {
+      const unsigned x = ~D[i];
+      D[i] = x + c;
+      c = (c && D[i] == 0) ? 1 : 0;
+    }
+  }
+  int top = 4;
+  while (top > 0 && D[top] == 0) --top;
+  if (D[top] == 0) return 0.0;
+  // take 64 bits starting at the top word
+  const int lz = __clz(D[top]);
+  unsigned long long hi = ((unsigned long long)D[top] << 32) | (top >= 1 ? D[top - 1] : 0u);
+  unsigned long long lo = top >= 2 ? ((unsigned long long)D[top - 2] << 32) : 0ull;
+  bool sticky = false;
+  for (int i = top - 3; i >= 0; --i) sticky |= (D[i] != 0);
+  // normalise: shift left by lz so bit 63 of hi is set
+  if (lz) { hi = (hi << lz) | (lo >> (64 - lz)); lo <<= lz; }
+  sticky |= (lo != 0);
+  // hi holds the top 64 bits; keep 53, round to nearest even
+  unsigned long long mant = hi >> 11;
+  const unsigned long long rem = hi & 0x7FFull;
+  const bool round_up = (rem > 0x400) || (rem == 0x400 && (sticky || (mant & 1)));
+  if (round_up) {
+    ++mant;
+    if (mant == (1ull << 53)) { mant >>= 1; ++sc; }  // carried into a new bit
+  }
+  // value = mant * 2^(e2), e2 = (bit index of hi's MSB) - 52 + sc
+  const int msb = 32 * top + 31 - lz;  // bit index of the leading one of D
+  int e2 = msb - 52 + sc;
+  const int expo = e2 + 52 + 1023;  // biased exponent of mant * 2^e2 (mant in [2^52, 2^53))
+  if (expo <= 0) return 0.0;       // underflow to zero (results this small are below FP64 noise)
+  if (expo >= 2047) return negv ? -INFINITY : INFINITY;
+  const unsigned long long bits = ((unsigned long long)expo << 52) | (mant & 0xFFFFFFFFFFFFFull) |
+                                  (negv ? 0x8000000000000000ull : 0ull);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double crt_value(const unsigned char* R, size_t stride, int sc) {
+  unsigned S[5] = {0, 0, 0, 0, 0};
+  float F = 0.f;
+#pragma unroll
+  for (int l = 0; l < NMOD; ++l) {
+    const unsigned c = R[(size_t)l * stride];
+    const unsigned W[4] = {c_W[l][0], c_W[l][1], c_W[l][2], c_W[l][3]};
+    mac160(S, c, W);
+    F = fmaf((float)c, c_frac[l], F);
+  }
+  const unsigned q = (unsigned)rintf(F);
+  // D = S - q M
+  unsigned qM[5] = {0, 0, 0, 0, 0};
+  const unsigned Mw[4] = {c_M[0], c_M[1], c_M[2], c_M[3]};
+  mac160(qM, q & 0xFFu, Mw);
+  if (q >> 8) {  // q < 2^12
+    unsigned t2[5] = {0, 0, 0, 0, 0};
+    mac160(t2, q >> 8, Mw);
+    // qM += t2 << 8
+    unsigned carry = 0;
+    unsigned sh[5];
+    sh[0] = t2[0] << 8;
+    for (int i = 1; i < 5; ++i) sh[i] = (t2[i] << 8) | (t2[i - 1] >> 24);
+    for (int i = 0; i < 5; ++i) {
+      unsigned long long s = (unsigned long long)qM[i] + sh[i] + carry;
+      qM[i] = (unsigned)s;
+      carry = (unsigned)(s >> 32);
+    }
+  }
+  unsigned D[5];
+  unsigned borrow = 0;
+  for (int i = 0; i < 5; ++i) {
+    const unsigned long long d = (unsigned long long)S[i] - qM[i] - borrow;
+    D[i] = (unsigned)d;
+    borrow = (unsigned)((d >> 63) & 1);
+  }
+  return int160_to_double(D, sc);
+}
+
+// C = alpha * (A B) + beta * C from the residues; one thread per element.
+__global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const int* ea, const int* eb, GemmArgs g,
+                                  int cplx) {
+  const size_t total = (size_t)M * N;
+  const int ncout = cplx ? 2 : 1;
+  const size_t stride = (size_t)ncout * total;
+  const bool beta0 = (g.beta.x == 0.0 && g.beta.y == 0.0);
+  const bool beta1 = (g.beta.x == 1.0 && g.beta.y == 0.0);
+  const bool alpha1 = (g.alpha.x == 1.0 && g.alpha.y == 0.0);
+  const bool alpham1 = (g.alpha.x == -1.0 && g.alpha.y == 0.0);
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % M), j = (int)(idx / M);
+    if (g.lower_only && i < j) continue;
+    const int sc = ea[i] + eb[j] - 104;
+    double vr = crt_value(Out + idx, stride, sc);
+    double vi = cplx ? crt_value(Out + total + idx, stride, sc) : 0.0;
+    double2 out;
+    if (alpha1) out = make_double2(vr, vi);
+    else if (alpham1) out = make_double2(-vr, -vi);
+    else out = cmul(g.alpha, make_double2(vr, vi));
+    const size_t ci = (size_t)i + (size_t)j * g.ldc;
+    if (cplx) {
+      double2* C = reinterpret_cast<double2*>(g.C);
+      if (beta1) out = cadd(out, C[ci]);
+      else if (!beta0) out = cadd(out, cmul(g.beta, C[ci]));
+      C[ci] = out;
+    } else {
+      double* C = reinterpret_cast<double*>(g.C);
+      double o = out.x;
+      if (beta1) o += C[ci];
+      else if (!beta0) o += g.beta.x * C[ci];
+      C[ci] = o;
+    }
+  }
+}
+
+size_t crt_bytes(int M, int N, int K, int cplx) {
+  const size_t Kp = (size_t)(K + CBK - 1) / CBK * CBK;
+  const int nc = cplx ? 3 : 1;
+  size_t b = 0;
+  b += (size_t)NMOD * nc * (size_t)M * Kp * 2 + 256;
+  b += (size_t)NMOD * nc * (size_t)N * Kp * 2 + 256;
+  b += (size_t)NMOD * (cplx ? 2 : 1) * (size_t)M * N + 256;
+  b += ((size_t)M + N) * sizeof(int) + 512;
+  return b;
+}
+
+Operand make_operand(const void* X, int ld, int R, int K, int op, bool isA, int cplx) {
+  Operand o;
+  o.X = X; o.ld = ld; o.R = R; o.K = K; o.cplx = cplx; o.cj = (op == OP_C) ? 1 : 0;
+  if (isA) o.mode = (op == OP_N) ? 0 : (op == OP_H ? 2 : 1);
+  else o.mode = (op == OP_N) ? 1 : 0;
+  return o;
+}
+
+}  // namespace
+
+size_t crt_gemm_ws_bytes(int M, int N, int K, int cplx) { return crt_bytes(M, N, K, cplx); }
+
+size_t crt_budget_bytes(int n) {
+  const int b = std::max(1, std::min(n, CRT_BLOCK));
+  return crt_bytes(b, b, b, 1);
+}
+
+int gemm(Ctx& c, const GemmArgs& g, int cplx) {
+  if (g.m <= 0 || g.n <= 0) return 0;
+  const double work = (double)g.m * g.n * std::max(g.k, 0);
+  const bool use_crt = c.engine == GBHE_ENGINE_CRT && c.crt_ws != nullptr && g.k >= 16 && work >= 2.0e6;
+  if (!use_crt) return cplx ? zgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes)
+                            : dgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes);
+  // blocks of at most CRT_BLOCK in every dimension; K blocks accumulate in C
+  const int bm = std::min(g.m, CRT_BLOCK), bn = std::min(g.n, CRT_BLOCK), bk = std::min(g.k, CRT_BLOCK);
+  const size_t es = cplx ? sizeof(cplx) : sizeof(double);
+  const bool herm = (g.opA == OP_H);
+  for (int k0 = 0; k0 < g.k; k0 += bk) {
+    const int kk = std::min(bk, g.k - k0);
+    for (int j0 = 0; j0 < g.n; j0 += bn) {
+      const int nn = std::min(bn, g.n - j0);
+      for (int i0 = 0; i0 < g.m; i0 += bm) {
+        const int mm = std::min(bm, g.m - i0);
+        if (g.lower_only && i0 + mm <= j0) continue;  // block strictly above the diagonal
+        GemmArgs s = g;
+        s.m = mm; s.n = nn; s.k = kk;
+        s.lower_only = (g.lower_only && i0 < j0 + nn) ? 1 : 0;
+        if (s.lower_only && (i0 != j0 || mm != nn)) return GBHE_EWORKSPACE;  // blocks are aligned squares
+        if (k0 > 0) s.beta = mk(1.0, 0.0);
+        // operand sub-blocks
+        const char* A = reinterpret_cast<const char*>(g.A);
+        const char* B = reinterpret_cast<const char*>(g.B);
+        if (herm) {
+          if (g.k != g.m) return GBHE_EWORKSPACE;
+          // op(A)(i0:i0+mm, k0:k0+kk) of a Hermitian matrix: Hermitian only on diagonal blocks
+          if (i0 == k0 && mm == kk) {
+            s.opA = OP_H;
+            s.A = A + ((size_t)i0 + (size_t)k0 * g.lda) * es;
+          } else if (i0 > k0) {
+            s.opA = OP_N;
+            s.A = A + ((size_t)i0 + (size_t)k0 * g.lda) * es;
+          } else {
+            s.opA = OP_C;  // stored lower block (k0.., i0..), conjugate-transposed
+            s.A = A + ((size_t)k0 + (size_t)i0 * g.lda) * es;
+          }
+        } else if (g.opA == OP_N) {
+          s.A = A + ((size_t)i0 + (size_t)k0 * g.lda) * es;
+        } else {
+          s.A = A + ((size_t)k0 + (size_t)i0 * g.lda) * es;
+        }
+        if (g.opB == OP_N) s.B = B + ((size_t)k0 + (size_t)j0 * g.ldb) * es;
+        else s.B = B + ((size_t)j0 + (size_t)k0 * g.ldb) * es;
+        s.C = reinterpret_cast<char*>(g.C) + ((size_t)i0 + (size_t)j0 * g.ldc) * es;
+        int rc = crt_gemm(c.st, s, cplx, c.crt_ws, c.crt_ws_bytes);
+        if (rc) return rc;
+      }
+    }
+  }
+  return 0;
+}
+
+int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes) {
+  if (g.m <= 0 || g.n <= 0) return 0;
+  if (g.k <= 0 || g.k > KMAX) return GBHE_EWORKSPACE;
+  int rc = init_constants();
+  if (rc) return rc;
+  const int M = g.m, N = g.n, K = g.k;
+  const int Kp = (K + CBK - 1) / CBK * CBK;
+  const int nc = cplx ? 3 : 1;
+  if (crt_bytes(M, N, K, cplx) > ws_bytes) return GBHE_EWORKSPACE;
+  char* p = reinterpret_cast<char*>(ws);
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
+  __half* PA = reinterpret_cast<__half*>(take((size_t)NMOD * nc * M * Kp * 2));
+  __half* PB = reinterpret_cast<__half*>(take((size_t)NMOD * nc * N * Kp * 2));
+  unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)NMOD * (cplx ? 2 : 1) * M * N));
+  int* ea = reinterpret_cast<int*>(take((size_t)M * sizeof(int)));
+  int* eb = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
+  const Operand oa = make_operand(g.A, g.lda, M, K, g.opA, true, cplx);
+  const Operand ob = make_operand(g.B, g.ldb, N, K, g.opB, false, cplx);
+  const double flops = (cplx ? 8.0 : 2.0) * (double)M * N * K;
+  ProfScope prof(st, GBHE_PROF_CRT, flops, 0.0);
+  k_fill_int<<<64, 256, 0, st>>>(ea, M, -1100);
+  count_launch();
+  k_fill_int<<<64, 256, 0, st>>>(eb, N, -1100);
+  count_launch();
+  k_op_exponents<<<dim3((M + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(oa, ea);
+  count_launch();
+  k_op_exponents<<<dim3((N + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(ob, eb);
+  count_launch();
+  k_op_residues<<<dim3((M + 31) / 32, Kp / 32), dim3(32, 8), 0, st>>>(oa, ea, Kp, PA);
+  count_launch();
+  k_op_residues<<<dim3((N + 31) / 32, Kp / 32), dim3(32, 8), 0, st>>>(ob, eb, Kp, PB);
+  count_launch();
+  const size_t smem = (size_t)CSTAGE * nc * (CBM + CBN) * KPAD * sizeof(__half);
+  static bool attr_c = false, attr_r = false;
+  dim3 grid((M + CBM - 1) / CBM, (N + CBN - 1) / CBN, NMOD);
+  if (cplx) {
+    if (!attr_c) {
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_c = true;
+    }
+    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out);
+  } else {
+    if (!attr_r) {
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_r = true;
+    }
+    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out);
+  }
+  count_launch();
+  const size_t total = (size_t)M * N;
+  k_crt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, M, N, ea, eb, g, cplx);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
+}
+
+}  // namespace gbhe

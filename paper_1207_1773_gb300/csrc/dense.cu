@@ -187,12 +187,12 @@ int potrf_run(Ctx& c, int n, cplx* B, int ldb) {
     if (rest <= 0) break;
     cplx* A21 = B + (size_t)(k0 + bs) + (size_t)k0 * ldb;
     // L21 = A21 * Linv^H   (in place: one 64-wide column block per CTA row)
-    rc = zgemm(c.st, gemm_args(OP_N, OP_C, rest, bs, bs, mk(1, 0), A21, ldb, Linv, DB, mk(0, 0), A21, ldb),
+    rc = zgemm(c, gemm_args(OP_N, OP_C, rest, bs, bs, mk(1, 0), A21, ldb, Linv, DB, mk(0, 0), A21, ldb),
                nullptr, 0);
     if (rc) return rc;
     // A22 -= L21 L21^H (lower)
     cplx* A22 = B + (size_t)(k0 + bs) + (size_t)(k0 + bs) * ldb;
-    rc = zgemm(c.st, gemm_args(OP_N, OP_C, rest, rest, bs, mk(-1, 0), A21, ldb, A21, ldb, mk(1, 0), A22, ldb, 1),
+    rc = zgemm(c, gemm_args(OP_N, OP_C, rest, rest, bs, mk(-1, 0), A21, ldb, A21, ldb, mk(1, 0), A22, ldb, 1),
                c.gemm_scratch, c.gemm_scratch_bytes);
     if (rc) return rc;
   }
@@ -213,12 +213,12 @@ int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, i
     for (int b = 0; b < nblk; ++b) {
       const int k0 = b * DB, bs = std::min(DB, n - k0);
       cplx* Xb = X + k0;
-      rc = zgemm(c.st, gemm_args(OP_N, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
+      rc = zgemm(c, gemm_args(OP_N, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
                                  mk(0, 0), Xb, ldx), nullptr, 0);
       if (rc) return rc;
       const int rest = n - k0 - bs;
       if (rest > 0) {
-        rc = zgemm(c.st, gemm_args(OP_N, OP_N, rest, m, bs, mk(-1, 0), L + (size_t)(k0 + bs) + (size_t)k0 * ldl, ldl,
+        rc = zgemm(c, gemm_args(OP_N, OP_N, rest, m, bs, mk(-1, 0), L + (size_t)(k0 + bs) + (size_t)k0 * ldl, ldl,
                                    Xb, ldx, mk(1, 0), X + k0 + bs, ldx), nullptr, 0);
         if (rc) return rc;
       }
@@ -227,12 +227,12 @@ int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, i
     for (int b = nblk - 1; b >= 0; --b) {
       const int k0 = b * DB, bs = std::min(DB, n - k0);
       cplx* Xb = X + k0;
-      rc = zgemm(c.st, gemm_args(OP_C, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
+      rc = zgemm(c, gemm_args(OP_C, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
                                  mk(0, 0), Xb, ldx), nullptr, 0);
       if (rc) return rc;
       if (k0 > 0) {
         // X[0:k0] -= L[k0:k0+bs, 0:k0]^H X_b
-        rc = zgemm(c.st, gemm_args(OP_C, OP_N, k0, m, bs, mk(-1, 0), L + k0, ldl, Xb, ldx, mk(1, 0), X, ldx),
+        rc = zgemm(c, gemm_args(OP_C, OP_N, k0, m, bs, mk(-1, 0), L + k0, ldl, Xb, ldx, mk(1, 0), X, ldx),
                    nullptr, 0);
         if (rc) return rc;
       }

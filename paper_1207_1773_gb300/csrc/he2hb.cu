@@ -215,14 +215,14 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
     cplx* A22 = A + (size_t)(k + nb) + (size_t)(k + nb) * lda;
     const cplx* T = pa.T;
     const cplx one = mk(1, 0), zero = mk(0, 0), mone = mk(-1, 0);
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, mp, kr, kr, one, V, n, T, nb, zero, VT, n), nullptr, 0))) break;
-    if ((rc = zgemm(c.st, gemm_args(OP_H, OP_N, mp, kr, mp, one, A22, lda, VT, n, zero, X, n), nullptr, 0))) break;
-    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, kr, kr, mp, one, V, n, X, n, zero, Ys, nb), c.gemm_scratch,
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, kr, kr, one, V, n, T, nb, zero, VT, n), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_H, OP_N, mp, kr, mp, one, A22, lda, VT, n, zero, X, n), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, kr, kr, mp, one, V, n, X, n, zero, Ys, nb), c.gemm_scratch,
                     c.gemm_scratch_bytes))) break;
-    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, kr, kr, kr, one, T, nb, Ys, nb, zero, Zs, nb), nullptr, 0))) break;
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, mp, kr, kr, mk(-0.5, 0), V, n, Zs, nb, one, X, n), nullptr, 0))) break;
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_C, mp, mp, kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0))) break;
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_C, mp, mp, kr, mone, X, n, V, n, one, A22, lda, 1), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, kr, kr, kr, one, T, nb, Ys, nb, zero, Zs, nb), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, kr, kr, mk(-0.5, 0), V, n, Zs, nb, one, X, n), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, kr, mone, X, n, V, n, one, A22, lda, 1), nullptr, 0))) break;
   }
   a.off = save;
   return rc;

@@ -14,10 +14,24 @@ struct Ctx {
   cplx* dense_scratch;        // diagonal-block inverses, ceil(n/64)*64*64
   void* gemm_scratch;         // split-K partial sums
   size_t gemm_scratch_bytes;
+  void* crt_ws;               // residue planes of the tensor-core FP64 GEMM
+  size_t crt_ws_bytes;
+  int engine;                 // GBHE_ENGINE_DMMA or GBHE_ENGINE_CRT
   Arena arena;                // the rest, for stage temporaries
 };
 
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(32) << 20;
+// Workspace of the tensor-core FP64 GEMM: enough for 4096 x 4096 x 4096
+// complex blocks; larger products are cut into blocks of that size.
+constexpr int CRT_BLOCK = 4096;
+size_t crt_budget_bytes(int n);
+
+// FP64 GEMM through the engine selected on the handle: exact modular products
+// on the FP16 tensor cores for large products, DMMA otherwise.
+int gemm(Ctx& c, const GemmArgs& g, int cplx);
+// Complex product through the engine selected on the handle (the scratch
+// arguments are kept for the DMMA split-K path, which uses the context's).
+inline int zgemm(Ctx& c, const GemmArgs& g, void*, size_t) { return gemm(c, g, 1); }
 
 // RAII marker for the optional profiler: records CUDA events around the
 // enclosed launches of class `cls` when profiling is on (prof.cu).
@@ -34,6 +48,10 @@ class ProfScope {
   int cls_;
   void* ev_;
 };
+
+// FP64-exact GEMM on the FP16 tensor cores (crt.cu); workspace passed explicitly.
+size_t crt_gemm_ws_bytes(int M, int N, int K, int cplx);
+int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes);
 
 size_t dense_ws_bytes(int n);
 int potrf_run(Ctx& c, int n, cplx* B, int ldb);

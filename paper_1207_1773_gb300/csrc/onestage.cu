@@ -278,9 +278,9 @@ static int hetrd_onestage(Ctx& c, int n, cplx* A, int lda, cplx* V, cplx* W, cpl
       cplx* A22 = A + (size_t)k2 + (size_t)k2 * lda;
       const int m2 = n - k2;
       int rc;
-      if ((rc = zgemm(c.st, gemm_args(OP_N, OP_C, m2, m2, jn, mone, V + k2, n, W + k2, n, one, A22, lda, 1),
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_C, m2, m2, jn, mone, V + k2, n, W + k2, n, one, A22, lda, 1),
                       nullptr, 0))) return rc;
-      if ((rc = zgemm(c.st, gemm_args(OP_N, OP_C, m2, m2, jn, mone, W + k2, n, V + k2, n, one, A22, lda, 1),
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_C, m2, m2, jn, mone, W + k2, n, V + k2, n, one, A22, lda, 1),
                       nullptr, 0))) return rc;
     }
   }
@@ -301,16 +301,16 @@ static int unmtr_onestage(Ctx& c, int n, int m, const cplx* A, int lda, const cp
     k_os_panel_v<<<(int)std::min<size_t>(((size_t)mp * jn + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, n, k, jn, V, n);
     count_launch();
     int rc;
-    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, jn, jn, mp, one, V, n, V, n, zero, G, NBT), c.gemm_scratch,
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, jn, jn, mp, one, V, n, V, n, zero, G, NBT), c.gemm_scratch,
                     c.gemm_scratch_bytes))) return rc;
     k_larft<<<1, 128, 0, c.st>>>(G, NBT, tau + k, jn, T);
     count_launch();
     cplx* Xr = X + (k + 1);
-    if ((rc = zgemm(c.st, gemm_args(OP_C, OP_N, jn, m, mp, one, V, n, Xr, ldx, zero, W1, NBT), c.gemm_scratch,
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, jn, m, mp, one, V, n, Xr, ldx, zero, W1, NBT), c.gemm_scratch,
                     c.gemm_scratch_bytes))) return rc;
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, jn, m, jn, one, T, NBT, W1, NBT, zero, W2, NBT), nullptr, 0)))
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, jn, m, jn, one, T, NBT, W1, NBT, zero, W2, NBT), nullptr, 0)))
       return rc;
-    if ((rc = zgemm(c.st, gemm_args(OP_N, OP_N, mp, m, jn, mone, V, n, W2, NBT, one, Xr, ldx), nullptr, 0)))
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, m, jn, mone, V, n, W2, NBT, one, Xr, ldx), nullptr, 0)))
       return rc;
   }
   return 0;

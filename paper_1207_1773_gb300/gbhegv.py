@@ -67,6 +67,9 @@ def _load():
             "gbhe_hegv_onestage": ([P, I, P, I, P, I, I, I, P, P, I, P], I),
             "gbhe_status_string": ([I], ctypes.c_char_p),
             "gbhe_zgemm": ([P, I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
+            "gbhe_crt_workspace_size": ([I, I, I, I, ctypes.POINTER(S)], I),
+            "gbhe_set_gemm_engine": ([P, I], I),
+            "gbhe_gemm_crt": ([P, I, I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
             "gbhe_launch_count": ([], ctypes.c_ulonglong),
             "gbhe_profile_enable": ([I], I),
             "gbhe_profile_read": ([I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_double),
@@ -91,7 +94,8 @@ def exported_symbols():
                         "gbhe_hb2st_sizes", "gbhe_hb2st", "gbhe_stedc", "gbhe_unmtr_2stage",
                         "gbhe_trsm_lh", "gbhe_hegv", "gbhe_hegv_onestage", "gbhe_status_string",
                         "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
-                        "gbhe_probe_fp64_peaks")]
+                        "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
+                        "gbhe_set_gemm_engine")]
 
 
 def status_string(code: int) -> str:
@@ -146,7 +150,9 @@ class Handle:
         return int(b.value)
 
     def ensure_workspace(self, n, nb=0, m=None):
-        need = self.workspace_size(n, nb, m)
+        return self.ensure_bytes(self.workspace_size(n, nb, m))
+
+    def ensure_bytes(self, need):
         if self.work is None or self.work_bytes < need:
             self.work = None
             torch.cuda.synchronize(self.device)
@@ -283,7 +289,7 @@ def trsm_lh(L, X):
     _check("gbhe_trsm_lh", _load().gbhe_trsm_lh(h.h, n, m, _ptr(L), _ld(L), _ptr(X), _ld(X), _stream(L.device)))
 
 
-PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6}
+PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6, "crt": 7}
 
 
 def launch_count() -> int:
@@ -313,6 +319,15 @@ def probe_fp64_peaks(device=0):
 
 
 OPS = {"N": 0, "T": 1, "C": 2, "H": 3}
+ENGINES = {"dmma": 0, "crt": 1}
+
+
+def set_engine(name, device=None):
+    """Engine of the FP64 level-3 products: 'crt' (FP16 tensor cores, exact
+    modular arithmetic; default) or 'dmma' (FP64 tensor pipe only)."""
+    h = handle(device)
+    _check("gbhe_set_gemm_engine", _load().gbhe_set_gemm_engine(h.h, ENGINES[name]))
+    h.engine = name
 
 
 def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
@@ -325,6 +340,23 @@ def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     _check("gbhe_zgemm", _load().gbhe_zgemm(h.h, OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag), _ptr(A),
                                             _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C), _ld(C),
                                             int(bool(lower)), _stream(C.device)))
+    return C
+
+
+def gemm_crt(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
+    """C = alpha op(A) op(B) + beta C computed exactly-modularly on the FP16
+    tensor cores (complex128 or float64 operands), in place."""
+    h = handle(C.device)
+    cplx = 1 if C.dtype == torch.complex128 else 0
+    m, n = C.shape
+    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    need = ctypes.c_size_t()
+    _check("gbhe_crt_workspace_size", _load().gbhe_crt_workspace_size(m, n, k, cplx, ctypes.byref(need)))
+    h.ensure_bytes(h.workspace_size(1) + int(need.value) + 4096)
+    a, b = complex(alpha), complex(beta)
+    _check("gbhe_gemm_crt", _load().gbhe_gemm_crt(h.h, cplx, OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag),
+                                                  _ptr(A), _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C),
+                                                  _ld(C), int(bool(lower)), _stream(C.device)))
     return C
 
 

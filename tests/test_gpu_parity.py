@@ -253,9 +253,16 @@ def _cluster_subspace_check(A, B, w, X, wo, Xo):
         i = j
 
 
+@pytest.fixture(params=["crt", "dmma"])
+def engine(G, request):
+    G.set_engine(request.param)
+    yield request.param
+    G.set_engine("crt")
+
+
 @pytest.mark.parametrize("n,nb,seed", [(1, 1, 0), (2, 1, 0), (5, 2, 1), (33, 8, 2), (64, 16, 3), (100, 32, 4),
-                                       (129, 16, 5), (256, 32, 0)])
-def test_hegv_all(G, n, nb, seed):
+                                       (129, 16, 5), (256, 32, 0), (700, 64, 6)])
+def test_hegv_all(G, engine, n, nb, seed):
     A, B, lam = inputs.make_pair(n, seed)
     w, X = G.hegv(_c(A), _c(B), 1, n, nb=nb)
     w, X = _np(w), _np(X)
