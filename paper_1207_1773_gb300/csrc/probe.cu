@@ -35,7 +35,11 @@ __global__ void k_probe_dmma(double* out) {
           : "d"(a0), "d"(a1), "d"(b));
     a0 += 1e-9;
   }
-  out[blockIdx.x * blockDim.x + threadIdx.x] = c[0][0] + c[1][1] + c[2][2] + c[3][3];
+  // every accumulator value is consumed: dead output rows let the compiler
+  // drop half of an m16n8k4 product and the rate would read twice too high
+  double s = 0.0;
+  for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1] + c[j][2] + c[j][3];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 }  // namespace
