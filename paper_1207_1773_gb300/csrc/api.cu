@@ -377,11 +377,12 @@ int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx a
   if (ldc < std::max(1, m)) return -14;
   if (opA == OP_H && m != k) return -2;
   Ctx c;
-  int rc = make_ctx(h, 1, stream, &c);
+  int rc = make_ctx(h, std::max(std::max(m, n), k), stream, &c);
   if (rc) return rc;
-  return zgemm(c.st, gemm_args(opA, opB, m, n, k, mk(alpha.re, alpha.im), A, lda, B, ldb, mk(beta.re, beta.im), C,
-                               ldc, lower),
-               c.gemm_scratch, c.gemm_scratch_bytes);
+  // through the engine selected on the handle (large products cut into blocks)
+  return gemm(c, gemm_args(opA, opB, m, n, k, mk(alpha.re, alpha.im), A, lda, B, ldb, mk(beta.re, beta.im), C, ldc,
+                           lower),
+              1);
 }
 
 int gbhe_crt_workspace_size(int m, int n, int k, int cplx, size_t* bytes) {

@@ -576,7 +576,8 @@ int gemm(Ctx& c, const GemmArgs& g, int cplx) {
                             : dgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes);
   // blocks of at most CRT_BLOCK in every dimension; K blocks accumulate in C
   const int bm = std::min(g.m, CRT_BLOCK), bn = std::min(g.n, CRT_BLOCK), bk = std::min(g.k, CRT_BLOCK);
-  const size_t es = cplx ? sizeof(cplx) : sizeof(double);
+  // element size in bytes (the int parameter `cplx` shadows the type name here)
+  const size_t es = cplx ? sizeof(double2) : sizeof(double);
   const bool herm = (g.opA == OP_H);
   for (int k0 = 0; k0 < g.k; k0 += bk) {
     const int kk = std::min(bk, g.k - k0);

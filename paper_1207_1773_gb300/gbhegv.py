@@ -331,11 +331,11 @@ def set_engine(name, device=None):
 
 
 def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
-    """C = alpha op(A) op(B) + beta C on the library's DMMA GEMM (in place)."""
+    """C = alpha op(A) op(B) + beta C through the library's GEMM engine (in place)."""
     h = handle(C.device)
-    h.ensure_workspace(1)
     m, n = C.shape
     k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    h.ensure_workspace(max(m, n, k), 1, 1)
     a, b = complex(alpha), complex(beta)
     _check("gbhe_zgemm", _load().gbhe_zgemm(h.h, OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag), _ptr(A),
                                             _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C), _ld(C),
