@@ -88,6 +88,101 @@ __global__ void __launch_bounds__(QT) k_apply_q2(int n, int nb, int m, int J, co
   }
 }
 
+// ---------------------------------------------------------------- Q2 as block reflectors
+// Diamond (b, j): the step-j reflectors of sweeps b*nb .. b*nb+nb-1.  Their
+// rows start at r0 = (b + j) nb + 1 (the reflector of sweep b*nb + c starts at
+// local row c), so the diamond is one block reflector on a (2nb-1)-row window:
+//   H(s0, j) H(s0+1, j) ... H(s0+nb-1, j) = I - V T V^H = I - U V^H,  U = V T,
+// T upper triangular from the forward recurrence.  Diamonds are numbered
+// gid = b J - b (b - 1) / 2 + j.  Applied in wavefront order
+// t = 2 (J - 1 - b) + j: diamonds of one step touch disjoint rows, and every
+// pair of overlapping diamonds is ordered as the sequential order requires
+// (later sweeps first; within a sweep group, step j ascending).
+__host__ __device__ inline long q2_gid(int b, int j, int J) { return (long)b * J - (long)b * (b - 1) / 2 + j; }
+
+__global__ void __launch_bounds__(256) k_q2_build(int n, int nb, int J, const cplx* V2, const cplx* tau2, cplx* Vg,
+                                                  cplx* Ug) {
+  extern __shared__ cplx sm[];
+  cplx* T = sm;            // nb x nb
+  cplx* G = sm + nb * nb;  // nb x nb (Gram V^H V)
+  __shared__ cplx tau_s[128];
+  const long gid = blockIdx.x;
+  int b = 0;
+  while (b + 1 < J && q2_gid(b + 1, 0, J) <= gid) ++b;
+  const int j = (int)(gid - q2_gid(b, 0, J));
+  const int s0 = b * nb, r0 = (b + j) * nb + 1, W2 = 2 * nb;
+  cplx* V = Vg + (size_t)gid * W2 * nb;
+  cplx* U = Ug + (size_t)gid * W2 * nb;
+  const int t = threadIdx.x;
+  // V (window rows x nb, ld 2nb): column c holds the reflector of sweep s0 + c at rows c.. c+L-1
+  for (int q = t; q < W2 * nb; q += blockDim.x) {
+    const int i = q % W2, c = q / W2, s = s0 + c;
+    cplx v = mk(0.0, 0.0);
+    if (s <= n - 2 && j < (n - 1 - s + nb - 1) / nb) {
+      const int a = s + 1 + j * nb, L = min(nb, n - a);
+      if (i >= c && i < c + L && r0 + i < n) v = V2[((size_t)s * J + j) * nb + (i - c)];
+    }
+    V[q] = v;
+  }
+  for (int c = t; c < nb; c += blockDim.x) {
+    const int s = s0 + c;
+    tau_s[c] = (s <= n - 2 && j < (n - 1 - s + nb - 1) / nb) ? tau2[(size_t)s * J + j] : mk(0.0, 0.0);
+  }
+  __syncthreads();
+  // Gram: G[q][c] = V(:,q)^H V(:,c) for q < c (overlap rows c .. q+nb-1)
+  for (int e = t; e < nb * nb; e += blockDim.x) {
+    const int q = e % nb, c = e / nb;
+    cplx acc = mk(0.0, 0.0);
+    if (q < c)
+      for (int i = c; i < min(q + nb, W2); ++i) ccfma(acc, V[i + (size_t)q * W2], V[i + (size_t)c * W2]);
+    G[q + c * nb] = acc;
+    T[q + c * nb] = mk(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    const cplx tc = tau_s[c];
+    // T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c)
+    for (int r = t; r < c; r += blockDim.x) {
+      cplx acc = mk(0.0, 0.0);
+      for (int q = r; q < c; ++q) cfma(acc, T[r + q * nb], G[q + c * nb]);
+      T[r + c * nb] = cscal(-1.0, cmul(tc, acc));
+    }
+    if (t == 0) T[c + c * nb] = tc;
+    __syncthreads();
+  }
+  // U = V T
+  for (int q = t; q < W2 * nb; q += blockDim.x) {
+    const int i = q % W2, c = q / W2;
+    cplx acc = mk(0.0, 0.0);
+    for (int k = max(0, i - nb + 1); k <= min(c, i); ++k) cfma(acc, V[i + (size_t)k * W2], T[k + c * nb]);
+    U[q] = acc;
+  }
+}
+
+// Descriptors of one wavefront step t for the batched products
+//   W_z = V_z^H X[r0 : r0+Wh, c0 : c0+mc]          (GEMM 1)
+//   X[r0 : r0+Wh, c0 : c0+mc] -= U_z W_z            (GEMM 2)
+__global__ void k_q2_desc(int n, int nb, int J, int t, int b_lo, int cnt, const cplx* Vg, const cplx* Ug, cplx* X,
+                          int ldx, int c0, int mc, cplx* Wbuf, CrtDesc* D1, CrtDesc* D2) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= cnt) return;
+  const int b = b_lo + z, j = t - 2 * (J - 1 - b);
+  const long gid = q2_gid(b, j, J);
+  const int r0 = (b + j) * nb + 1, Wh = min(2 * nb - 1, n - r0), W2 = 2 * nb;
+  cplx* Wz = Wbuf + (size_t)z * nb * mc;
+  CrtDesc d;
+  d.A = Vg + (size_t)gid * W2 * nb; d.lda = W2;
+  d.B = X + (size_t)r0 + (size_t)c0 * ldx; d.ldb = ldx;
+  d.C = Wz; d.ldc = nb;
+  d.M = nb; d.N = mc; d.K = Wh;
+  D1[z] = d;
+  d.A = Ug + (size_t)gid * W2 * nb; d.lda = W2;
+  d.B = Wz; d.ldb = nb;
+  d.C = X + (size_t)r0 + (size_t)c0 * ldx; d.ldc = ldx;
+  d.M = Wh; d.N = mc; d.K = nb;
+  D2[z] = d;
+}
+
 // Explicit V of panel p (mp x kr, ld ldv): unit diagonal, zeros above, the
 // stored reflectors below.
 __global__ void k_panel_v(const cplx* A, int lda, int k, int nb, int mp, int kr, cplx* V, int ldv) {
@@ -106,9 +201,95 @@ __global__ void k_panel_v(const cplx* A, int lda, int k, int nb, int mp, int kr,
 
 }  // namespace
 
+namespace {
+
+// Largest number of diamonds in one wavefront step.
+int q2_max_step(int J) {
+  int best = 0;
+  for (int t = 0; t <= 3 * J - 3; ++t) {
+    int cnt = 0;
+    for (int b = 0; b < J; ++b) {
+      const int j = t - 2 * (J - 1 - b);
+      if (j >= 0 && j < J - b) ++cnt;
+    }
+    best = std::max(best, cnt);
+  }
+  return best;
+}
+
+bool q2_use_blocks(const Ctx& c, int n, int nb) {
+  return c.engine == GBHE_ENGINE_CRT && c.crt_ws != nullptr && nb >= 2 && nb <= 64 && n > 2 * nb;
+}
+
+size_t q2_block_bytes(int n, int nb, int m) {
+  const int J = hb2st_J(n, nb);
+  const size_t ng = (size_t)J * (J + 1) / 2;
+  const size_t cm = (size_t)q2_max_step(J) + 1;
+  return 2 * ng * 2 * nb * nb * sizeof(cplx) + cm * nb * (size_t)std::max(m, 1) * sizeof(cplx) +
+         2 * cm * sizeof(CrtDesc) + 4 * 256;
+}
+
+}  // namespace
+
 size_t unmtr_ws_bytes(int n, int nb, int m) {
   const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max(m, 1);
-  return nn * nb * sizeof(cplx) + 2 * (size_t)nb * mm * sizeof(cplx) + 3 * 256;
+  size_t b = nn * nb * sizeof(cplx) + 2 * (size_t)nb * mm * sizeof(cplx) + 3 * 256;
+  if (nb >= 2 && nb <= 64 && n > 2 * nb) b += q2_block_bytes(n, nb, m);
+  return b;
+}
+
+// Q2 applied as wavefront-batched block reflectors on the tensor-core GEMM.
+static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const cplx* tau2, cplx* X, int ldx) {
+  Arena& ar = c.arena;
+  const size_t save = ar.off;
+  const int J = hb2st_J(n, nb);
+  const long ng = (long)J * (J + 1) / 2;
+  const int cm = q2_max_step(J);
+  const int W2 = 2 * nb;
+  cplx* Vg = ar.take<cplx>((size_t)ng * W2 * nb);
+  cplx* Ug = ar.take<cplx>((size_t)ng * W2 * nb);
+  // column chunk so that one batched product fits the tensor-core workspace
+  int mc = std::min(m, 64 * ((m + 63) / 64));
+  while (mc > 64 && crt_batched_ws_bytes(cm, W2, mc, W2, 1) > c.crt_ws_bytes) mc -= 64;
+  mc = std::min(mc, m);
+  cplx* Wbuf = ar.take<cplx>((size_t)std::max(cm, 1) * nb * mc);
+  CrtDesc* D1 = ar.take<CrtDesc>((size_t)std::max(cm, 1));
+  CrtDesc* D2 = ar.take<CrtDesc>((size_t)std::max(cm, 1));
+  if (!ar.ok() || !D2) { ar.off = save; return GBHE_EWORKSPACE; }
+  const size_t smem = (size_t)2 * nb * nb * sizeof(cplx);
+  GBHE_CUDA(cudaFuncSetAttribute(k_q2_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  double fl = 0.0;
+  if (prof_on())
+    for (int s = 0; s <= n - 2; ++s)
+      for (int a0 = s + 1; a0 < n; a0 += nb) fl += 16.0 * std::min(nb, n - a0) * (double)m;
+  ProfScope prof(c.st, GBHE_PROF_Q2, fl, 16.0 * ((double)n * J * nb + 2.0 * (double)n * m));
+  k_q2_build<<<(unsigned)ng, 256, smem, c.st>>>(n, nb, J, V2, tau2, Vg, Ug);
+  count_launch();
+  GBHE_CUDA(cudaGetLastError());
+  int rc = 0;
+  for (int c0 = 0; c0 < m && !rc; c0 += mc) {
+    const int mcc = std::min(mc, m - c0);
+    for (int t = 0; t <= 3 * J - 3 && !rc; ++t) {
+      int b_lo = -1, cnt = 0;
+      for (int b = 0; b < J; ++b) {
+        const int j = t - 2 * (J - 1 - b);
+        if (j >= 0 && j < J - b) {
+          if (b_lo < 0) b_lo = b;
+          ++cnt;
+        }
+      }
+      if (cnt == 0) continue;
+      k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, t, b_lo, cnt, Vg, Ug, X, ldx, c0, mcc, Wbuf, D1, D2);
+      count_launch();
+      rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, nb, mcc, W2 - 1, c.crt_ws,
+                            c.crt_ws_bytes);
+      if (!rc)
+        rc = crt_gemm_batched(c.st, OP_N, OP_N, mk(-1, 0), mk(1, 0), 1, D2, cnt, W2 - 1, mcc, nb, c.crt_ws,
+                              c.crt_ws_bytes);
+    }
+  }
+  ar.off = save;
+  return rc;
 }
 
 int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx* T1, const cplx* V2,
@@ -125,7 +306,10 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
   count_launch();
   GBHE_CUDA(cudaGetLastError());
   // ---- Q2
-  if (n >= 2) {
+  if (q2_use_blocks(c, n, nb)) {
+    int rc = apply_q2_blocks(c, n, nb, m, V2, tau2, X, ldx);
+    if (rc) { ar.off = save; return rc; }
+  } else if (n >= 2) {
     const int J = hb2st_J(n, nb);
     const size_t smem = (size_t)(2 * nb * SLAB + 2 * nb) * sizeof(cplx);
     if (smem > 48 * 1024)

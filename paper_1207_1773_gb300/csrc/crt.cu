@@ -125,9 +125,10 @@ __device__ __forceinline__ int exp_bound(double x) {
 
 // Max exponent per r over k.  Tile 32 (r) x 32 (k) per block of 32 x 8
 // threads; the contiguous storage direction maps to threadIdx.x.
-__global__ void k_op_exponents(Operand o, int* e) {
+__device__ __forceinline__ void op_exponents_tile(const Operand& o, int* e, int bx, int by) {
   __shared__ int tile[32][33];
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int r0 = bx * 32, k0 = by * 32;
+  if (r0 >= o.R || k0 >= o.K) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool r_contig = (o.mode == 0) || (o.mode == 2 && r0 >= k0 + 31);
   for (int q = ty; q < 32; q += 8) {
@@ -148,6 +149,8 @@ __global__ void k_op_exponents(Operand o, int* e) {
   }
 }
 
+__global__ void k_op_exponents(Operand o, int* e) { op_exponents_tile(o, e, blockIdx.x, blockIdx.y); }
+
 __global__ void k_fill_int(int* p, int n, int v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
@@ -163,9 +166,10 @@ __device__ __forceinline__ float fmod_small(float x, float p, float pinv) {
 
 // Residue planes: P[(l * ncomp + c) * R * Kp + r * Kp + k] (fp16), symmetric
 // residues of the scaled integer of element (r, k); zero for k >= K.
-__global__ void k_op_residues(Operand o, const int* e, int Kp, __half* P) {
+__device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e, int Kp, __half* P, int bx, int by) {
   __shared__ double2 tile[32][33];
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int r0 = bx * 32, k0 = by * 32;
+  if (r0 >= o.R || k0 >= Kp) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool r_contig = (o.mode == 0) || (o.mode == 2 && r0 >= k0 + 31);
   for (int q = ty; q < 32; q += 8) {
@@ -228,6 +232,41 @@ __global__ void k_op_residues(Operand o, const int* e, int Kp, __half* P) {
   }
 }
 
+__global__ void k_op_residues(Operand o, const int* e, int Kp, __half* P) {
+  op_residues_tile(o, e, Kp, P, blockIdx.x, blockIdx.y);
+}
+
+// ---- batched forms: entry z of a device descriptor array per blockIdx.z
+__device__ __forceinline__ Operand desc_operand(const CrtDesc& d, int isA, int op, int cplx) {
+  Operand o;
+  o.cplx = cplx;
+  o.cj = (op == OP_C) ? 1 : 0;
+  if (isA) {
+    o.X = d.A; o.ld = d.lda; o.R = d.M; o.K = d.K;
+    o.mode = (op == OP_N) ? 0 : (op == OP_H ? 2 : 1);
+  } else {
+    o.X = d.B; o.ld = d.ldb; o.R = d.N; o.K = d.K;
+    o.mode = (op == OP_N) ? 1 : 0;
+  }
+  return o;
+}
+
+__global__ void k_bop_exponents(const CrtDesc* D, int isA, int op, int cplx, int maxR, int* e) {
+  const Operand o = desc_operand(D[blockIdx.z], isA, op, cplx);
+  op_exponents_tile(o, e + (size_t)blockIdx.z * maxR, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_bop_residues(const CrtDesc* D, int isA, int op, int cplx, int maxR, const int* e, int Kp,
+                               __half* P) {
+  const Operand o = desc_operand(D[blockIdx.z], isA, op, cplx);
+  const size_t entry = (size_t)NMOD * (cplx ? 3 : 1) * maxR * Kp;
+  op_residues_tile(o, e + (size_t)blockIdx.z * maxR, Kp, P + blockIdx.z * entry, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_fill_int_batched(int* p, size_t n, int v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
 // ------------------------------------------------------------------ residue products
 __device__ __forceinline__ void cp16(void* smem, const void* g, bool pred) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -261,15 +300,28 @@ __device__ __forceinline__ float fmod_acc(float x, float p, float pinv) {
 // grid (ceil(M/CBM), ceil(N/CBN), NMOD); 8 warps as 4 (M) x 2 (N), warp tile 32 x 32.
 // PA: residue planes of op(A) (R = M), PB: of op(B) (R = N); both K-padded to Kp.
 // Out: bytes [l][comp][j][i] (column-major per plane), comp = re (and im).
+// Batched form (D != nullptr): blockIdx.z = entry * NMOD + modulus; entry
+// regions of the planes and outputs are sized for maxM / maxN, the layout
+// inside an entry uses the entry's own M, N.
 template <bool CPLX>
 __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __half* PB, int M, int N, int Kp,
-                                                   unsigned char* Out) {
+                                                   unsigned char* Out, const CrtDesc* D, int maxM, int maxN) {
   constexpr int NC = CPLX ? 3 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __half* sm = reinterpret_cast<__half*>(smem_raw);
   constexpr int A_ST = NC * CBM * KPAD, B_ST = NC * CBN * KPAD, ST = A_ST + B_ST;
-  const int l = blockIdx.z;
+  int l = blockIdx.z;
+  if (D) {
+    const int entry = blockIdx.z / NMOD;
+    l = blockIdx.z % NMOD;
+    M = D[entry].M;
+    N = D[entry].N;
+    PA += (size_t)entry * NMOD * NC * maxM * Kp;
+    PB += (size_t)entry * NMOD * NC * maxN * Kp;
+    Out += (size_t)entry * NMOD * (CPLX ? 2 : 1) * maxM * maxN;
+  }
   const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
+  if (m0 >= M || n0 >= N) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int wm = (w & 3) * 32, wn = (w >> 2) * 32;
   const float p = (float)c_p[l], pinv = c_pinv[l];
@@ -540,6 +592,47 @@ __global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const 
   }
 }
 
+// Batched reconstruction: C_z = alpha (A_z B_z) + beta C_z for every entry z.
+__global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, int nbatch, int maxM, int maxN,
+                                   const int* ea, const int* eb, double2 alpha, double2 beta, int cplx) {
+  const size_t per = (size_t)maxM * maxN;
+  const size_t total = per * nbatch;
+  const int ncout = cplx ? 2 : 1;
+  const bool beta0 = (beta.x == 0.0 && beta.y == 0.0);
+  const bool beta1 = (beta.x == 1.0 && beta.y == 0.0);
+  const bool alpha1 = (alpha.x == 1.0 && alpha.y == 0.0);
+  const bool alpham1 = (alpha.x == -1.0 && alpha.y == 0.0);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(q / per);
+    const size_t r = q % per;
+    const CrtDesc d = D[z];
+    const int i = (int)(r % maxM), j = (int)(r / maxM);
+    if (i >= d.M || j >= d.N) continue;
+    const size_t tot = (size_t)d.M * d.N, idx = (size_t)i + (size_t)j * d.M;
+    const unsigned char* O = Out + (size_t)z * NMOD * ncout * per;
+    const int sc = ea[(size_t)z * maxM + i] + eb[(size_t)z * maxN + j] - 104;
+    const double vr = crt_value(O + idx, (size_t)ncout * tot, sc);
+    const double vi = cplx ? crt_value(O + tot + idx, (size_t)ncout * tot, sc) : 0.0;
+    double2 out;
+    if (alpha1) out = make_double2(vr, vi);
+    else if (alpham1) out = make_double2(-vr, -vi);
+    else out = cmul(alpha, make_double2(vr, vi));
+    const size_t ci = (size_t)i + (size_t)j * d.ldc;
+    if (cplx) {
+      double2* C = reinterpret_cast<double2*>(d.C);
+      if (beta1) out = cadd(out, C[ci]);
+      else if (!beta0) out = cadd(out, cmul(beta, C[ci]));
+      C[ci] = out;
+    } else {
+      double* C = reinterpret_cast<double*>(d.C);
+      double o = out.x;
+      if (beta1) o += C[ci];
+      else if (!beta0) o += beta.x * C[ci];
+      C[ci] = o;
+    }
+  }
+}
+
 size_t crt_bytes(int M, int N, int K, int cplx) {
   const size_t Kp = (size_t)(K + CBK - 1) / CBK * CBK;
   const int nc = cplx ? 3 : 1;
@@ -562,6 +655,72 @@ Operand make_operand(const void* X, int ld, int R, int K, int op, bool isA, int 
 }  // namespace
 
 size_t crt_gemm_ws_bytes(int M, int N, int K, int cplx) { return crt_bytes(M, N, K, cplx); }
+
+size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) {
+  const size_t Kp = (size_t)(maxK + CBK - 1) / CBK * CBK;
+  const int nc = cplx ? 3 : 1;
+  const size_t nbt = (size_t)std::max(nbatch, 1);
+  size_t b = 0;
+  b += nbt * NMOD * nc * (size_t)maxM * Kp * 2 + 256;
+  b += nbt * NMOD * nc * (size_t)maxN * Kp * 2 + 256;
+  b += nbt * NMOD * (cplx ? 2 : 1) * (size_t)maxM * maxN + 256;
+  b += nbt * ((size_t)maxM + maxN) * sizeof(int) + 512;
+  return b;
+}
+
+int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, int cplx_flag, const CrtDesc* D,
+                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes) {
+  if (nbatch <= 0 || maxM <= 0 || maxN <= 0 || maxK <= 0) return 0;
+  if (maxK > KMAX || nbatch > 65535 / NMOD) return GBHE_EWORKSPACE;
+  if (crt_batched_ws_bytes(nbatch, maxM, maxN, maxK, cplx_flag) > ws_bytes) return GBHE_EWORKSPACE;
+  int rc = init_constants();
+  if (rc) return rc;
+  const int Kp = (maxK + CBK - 1) / CBK * CBK;
+  const int nc = cplx_flag ? 3 : 1;
+  char* p = reinterpret_cast<char*>(ws);
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
+  __half* PA = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxM * Kp * 2));
+  __half* PB = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxN * Kp * 2));
+  unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)nbatch * NMOD * (cplx_flag ? 2 : 1) * maxM * maxN));
+  int* ea = reinterpret_cast<int*>(take((size_t)nbatch * maxM * sizeof(int)));
+  int* eb = reinterpret_cast<int*>(take((size_t)nbatch * maxN * sizeof(int)));
+  ProfScope prof(st, GBHE_PROF_CRT, 0.0, 0.0);
+  k_fill_int_batched<<<256, 256, 0, st>>>(ea, (size_t)nbatch * maxM, -1100);
+  count_launch();
+  k_fill_int_batched<<<256, 256, 0, st>>>(eb, (size_t)nbatch * maxN, -1100);
+  count_launch();
+  k_bop_exponents<<<dim3((maxM + 31) / 32, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, 1, opA, cplx_flag, maxM, ea);
+  count_launch();
+  k_bop_exponents<<<dim3((maxN + 31) / 32, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, 0, opB, cplx_flag, maxN, eb);
+  count_launch();
+  k_bop_residues<<<dim3((maxM + 31) / 32, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, 1, opA, cplx_flag, maxM, ea, Kp, PA);
+  count_launch();
+  k_bop_residues<<<dim3((maxN + 31) / 32, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, 0, opB, cplx_flag, maxN, eb, Kp, PB);
+  count_launch();
+  const size_t smem = (size_t)CSTAGE * nc * (CBM + CBN) * KPAD * sizeof(__half);
+  static bool attr_c = false, attr_r = false;
+  dim3 grid((maxM + CBM - 1) / CBM, (maxN + CBN - 1) / CBN, NMOD * nbatch);
+  if (cplx_flag) {
+    if (!attr_c) {
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_c = true;
+    }
+    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN);
+  } else {
+    if (!attr_r) {
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_r = true;
+    }
+    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN);
+  }
+  count_launch();
+  const size_t total = (size_t)nbatch * maxM * maxN;
+  k_bcrt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, D, nbatch, maxM, maxN,
+                                                                                           ea, eb, alpha, beta,
+                                                                                           cplx_flag);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
+}
 
 size_t crt_budget_bytes(int n) {
   const int b = std::max(1, std::min(n, CRT_BLOCK));
@@ -663,13 +822,13 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_c = true;
     }
-    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out);
+    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, 0, 0);
   } else {
     if (!attr_r) {
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_r = true;
     }
-    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out);
+    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, 0, 0);
   }
   count_launch();
   const size_t total = (size_t)M * N;

@@ -53,6 +53,20 @@ class ProfScope {
 size_t crt_gemm_ws_bytes(int M, int N, int K, int cplx);
 int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes);
 
+// Batched form: entry z computes C_z = alpha op(A_z) op(B_z) + beta C_z with
+// its own sizes (M_z <= maxM, N_z <= maxN, K_z <= maxK) and pointers; the
+// descriptor array lives in device memory.  Operand modes, alpha and beta are
+// shared by all entries.
+struct CrtDesc {
+  const void* A;
+  const void* B;
+  void* C;
+  int M, N, K, lda, ldb, ldc;
+};
+size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx);
+int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, int cplx_flag, const CrtDesc* d_desc,
+                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes);
+
 size_t dense_ws_bytes(int n);
 int potrf_run(Ctx& c, int n, cplx* B, int ldb);
 int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, int ldx);
