@@ -16,7 +16,7 @@ constexpr int DT = 256;     // threads of the diagonal-block kernels
 // Factor the diagonal block A[k0:k0+bs, k0:k0+bs] (lower) in place and write
 // the inverse of its Cholesky factor to Linv (bs x bs, ld DB).
 __global__ void __launch_bounds__(DT) k_potrf_diag(cplx* A, int lda, int k0, int bs, cplx* Linv,
-                                                   int* st) {
+                                                   int* st, int info_off) {
   extern __shared__ cplx sm[];
   cplx* L = sm;              // DB x DB, ld DB
   cplx* X = sm + DB * DB;    // inverse
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(DT) k_potrf_diag(cplx* A, int lda, int k0, int
     if (t == 0) {
       double d = L[j + j * DB].x;
       if (!(d > 0.0) || !isfinite(d)) {
-        if (!bad) set_info_once(st, k0 + j + 1);
+        if (!bad) set_info_once(st, info_off + k0 + j + 1);
         bad = 1;
         d = 1.0;  // keep going on a harmless value; the status word carries the failure
       }
@@ -168,73 +168,166 @@ inline int grid1d(size_t total, int threads = 256) {
 
 }  // namespace
 
+// Outer blocking: the level-3 updates use TB = 256 columns (the tensor-core
+// GEMM is several times faster at K = 256 than at K = 64); the TB x TB
+// diagonal blocks are factored / inverted with the 64-wide kernels above.
+constexpr int TB = 256;
+
+// Layout of the dense scratch: 64-block inverses | TB-block inverses | temp.
+size_t inv64_elems(int n) { return (size_t)((n + DB - 1) / DB) * DB * DB; }
+size_t invtb_elems(int n) { return (size_t)((n + TB - 1) / TB) * TB * TB; }
+
 size_t dense_ws_bytes(int n) {
-  size_t nblk = (size_t)(n + DB - 1) / DB;
-  return nblk * DB * DB * sizeof(cplx) + 256;
+  const size_t nn = (size_t)std::max(n, 1);
+  return (inv64_elems(n) + invtb_elems(n) + nn * TB) * sizeof(cplx) + 3 * 256;
 }
 
-int potrf_run(Ctx& c, int n, cplx* B, int ldb) {
-  if (n <= 0) return 0;
-  int rc = ensure_attrs();
-  if (rc) return rc;
-  cplx* Linv = c.dense_scratch;
+namespace {
+
+cplx* inv64_buf(Ctx& c) { return c.dense_scratch; }
+cplx* invtb_buf(Ctx& c, int n) { return c.dense_scratch + inv64_elems(n); }
+cplx* temp_buf(Ctx& c, int n) { return c.dense_scratch + inv64_elems(n) + invtb_elems(n); }
+
+__global__ void k_set_identity(cplx* X, int ldx, int bs) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < bs * bs; q += gridDim.x * blockDim.x) {
+    const int r = q % bs, cc = q / bs;
+    X[(size_t)r + (size_t)cc * ldx] = mk(r == cc ? 1.0 : 0.0, 0.0);
+  }
+}
+
+__global__ void k_copy_block(const cplx* S, int lds, cplx* D, int ldd, int rows, int cols) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q % rows), cc = (int)(q / rows);
+    D[(size_t)r + (size_t)cc * ldd] = S[(size_t)r + (size_t)cc * lds];
+  }
+}
+
+// 64-blocked Cholesky of the n x n block B (info reported at offset info_off).
+int potrf64(Ctx& c, int n, cplx* B, int ldb, int info_off) {
+  cplx* Linv = inv64_buf(c);
   for (int k0 = 0; k0 < n; k0 += DB) {
     const int bs = std::min(DB, n - k0);
-    k_potrf_diag<<<1, DT, diag_smem(), c.st>>>(B, ldb, k0, bs, Linv, c.status);
+    k_potrf_diag<<<1, DT, diag_smem(), c.st>>>(B, ldb, k0, bs, Linv, c.status, info_off);
     count_launch();
     GBHE_CUDA(cudaGetLastError());
     const int rest = n - k0 - bs;
     if (rest <= 0) break;
     cplx* A21 = B + (size_t)(k0 + bs) + (size_t)k0 * ldb;
-    // L21 = A21 * Linv^H   (in place: one 64-wide column block per CTA row)
-    rc = zgemm(c, gemm_args(OP_N, OP_C, rest, bs, bs, mk(1, 0), A21, ldb, Linv, DB, mk(0, 0), A21, ldb),
-               nullptr, 0);
+    // L21 = A21 * Linv^H   (in place: N = 64 is one column tile of every engine)
+    int rc = zgemm(c, gemm_args(OP_N, OP_C, rest, bs, bs, mk(1, 0), A21, ldb, Linv, DB, mk(0, 0), A21, ldb), nullptr, 0);
     if (rc) return rc;
-    // A22 -= L21 L21^H (lower)
     cplx* A22 = B + (size_t)(k0 + bs) + (size_t)(k0 + bs) * ldb;
     rc = zgemm(c, gemm_args(OP_N, OP_C, rest, rest, bs, mk(-1, 0), A21, ldb, A21, ldb, mk(1, 0), A22, ldb, 1),
-               c.gemm_scratch, c.gemm_scratch_bytes);
+               nullptr, 0);
     if (rc) return rc;
   }
   return 0;
 }
 
-// X (n x m) := L^{-1} X (trans = 0) or L^{-H} X (trans = 1).
+// Inverse of the lower-triangular bs x bs block L (bs <= TB) into Linv (ld TB),
+// by the 64-blocked forward solve L X = I.
+int trtri_block(Ctx& c, int bs, const cplx* L, int ldl, cplx* Linv) {
+  k_set_identity<<<64, 256, 0, c.st>>>(Linv, TB, bs);
+  count_launch();
+  const int nb64 = (bs + DB - 1) / DB;
+  cplx* I64 = inv64_buf(c);
+  k_trtri_diag<<<nb64, DT, diag_smem(), c.st>>>(L, ldl, bs, I64);
+  count_launch();
+  GBHE_CUDA(cudaGetLastError());
+  for (int b = 0; b < nb64; ++b) {
+    const int k0 = b * DB, b64 = std::min(DB, bs - k0);
+    cplx* Xb = Linv + k0;
+    // rows k0.. of X: X_b = inv64 * X_b (M = 64 <= one row tile: in place is safe)
+    int rc = zgemm(c, gemm_args(OP_N, OP_N, b64, bs, b64, mk(1, 0), I64 + (size_t)b * DB * DB, DB, Xb, TB, mk(0, 0),
+                                Xb, TB), nullptr, 0);
+    if (rc) return rc;
+    const int rest = bs - k0 - b64;
+    if (rest > 0) {
+      rc = zgemm(c, gemm_args(OP_N, OP_N, rest, bs, b64, mk(-1, 0), L + (size_t)(k0 + b64) + (size_t)k0 * ldl, ldl, Xb,
+                              TB, mk(1, 0), Linv + k0 + b64, TB), nullptr, 0);
+      if (rc) return rc;
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
+int potrf_run(Ctx& c, int n, cplx* B, int ldb) {
+  if (n <= 0) return 0;
+  int rc = ensure_attrs();
+  if (rc) return rc;
+  cplx* Linv = invtb_buf(c, n);
+  cplx* T = temp_buf(c, n);
+  for (int k0 = 0; k0 < n; k0 += TB) {
+    const int bs = std::min(TB, n - k0);
+    cplx* Bkk = B + (size_t)k0 + (size_t)k0 * ldb;
+    if ((rc = potrf64(c, bs, Bkk, ldb, k0))) return rc;
+    const int rest = n - k0 - bs;
+    if (rest <= 0) break;
+    if ((rc = trtri_block(c, bs, Bkk, ldb, Linv))) return rc;
+    cplx* A21 = B + (size_t)(k0 + bs) + (size_t)k0 * ldb;
+    // L21 = A21 Linv^H  (through a temporary: N = TB spans several column tiles)
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, rest, bs, bs, mk(1, 0), A21, ldb, Linv, TB, mk(0, 0), T, rest), nullptr,
+                    0)))
+      return rc;
+    k_copy_block<<<1024, 256, 0, c.st>>>(T, rest, A21, ldb, rest, bs);
+    count_launch();
+    // A22 -= L21 L21^H (lower)
+    cplx* A22 = B + (size_t)(k0 + bs) + (size_t)(k0 + bs) * ldb;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, rest, rest, bs, mk(-1, 0), A21, ldb, A21, ldb, mk(1, 0), A22, ldb, 1),
+                    nullptr, 0)))
+      return rc;
+  }
+  return 0;
+}
+
+// X (n x m) := L^{-1} X (trans = 0) or L^{-H} X (trans = 1), TB-blocked.
 int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, int ldx) {
   if (n <= 0 || m <= 0) return 0;
   int rc = ensure_attrs();
   if (rc) return rc;
-  const int nblk = (n + DB - 1) / DB;
-  cplx* Linv = c.dense_scratch;
-  k_trtri_diag<<<nblk, DT, diag_smem(), c.st>>>(L, ldl, n, Linv);
-  count_launch();
-  GBHE_CUDA(cudaGetLastError());
-  if (trans == 0) {
-    for (int b = 0; b < nblk; ++b) {
-      const int k0 = b * DB, bs = std::min(DB, n - k0);
-      cplx* Xb = X + k0;
-      rc = zgemm(c, gemm_args(OP_N, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
-                                 mk(0, 0), Xb, ldx), nullptr, 0);
-      if (rc) return rc;
-      const int rest = n - k0 - bs;
-      if (rest > 0) {
-        rc = zgemm(c, gemm_args(OP_N, OP_N, rest, m, bs, mk(-1, 0), L + (size_t)(k0 + bs) + (size_t)k0 * ldl, ldl,
-                                   Xb, ldx, mk(1, 0), X + k0 + bs, ldx), nullptr, 0);
-        if (rc) return rc;
+  const int nblk = (n + TB - 1) / TB;
+  cplx* Linv = invtb_buf(c, n);
+  for (int b = 0; b < nblk; ++b) {
+    const int k0 = b * TB, bs = std::min(TB, n - k0);
+    if ((rc = trtri_block(c, bs, L + (size_t)k0 + (size_t)k0 * ldl, ldl, Linv + (size_t)b * TB * TB))) return rc;
+  }
+  cplx* T = temp_buf(c, n);
+  // the temporary holds TB x mc; process the columns in chunks of mc
+  const int mc = std::max(1, std::min(m, (int)(((size_t)std::max(n, 1) * TB) / TB)));
+  for (int c0 = 0; c0 < m; c0 += mc) {
+    const int mm = std::min(mc, m - c0);
+    cplx* Xc = X + (size_t)c0 * ldx;
+    if (trans == 0) {
+      for (int b = 0; b < nblk; ++b) {
+        const int k0 = b * TB, bs = std::min(TB, n - k0);
+        cplx* Xb = Xc + k0;
+        if ((rc = zgemm(c, gemm_args(OP_N, OP_N, bs, mm, bs, mk(1, 0), Linv + (size_t)b * TB * TB, TB, Xb, ldx,
+                                     mk(0, 0), T, TB), nullptr, 0)))
+          return rc;
+        k_copy_block<<<1024, 256, 0, c.st>>>(T, TB, Xb, ldx, bs, mm);
+        count_launch();
+        const int rest = n - k0 - bs;
+        if (rest > 0)
+          if ((rc = zgemm(c, gemm_args(OP_N, OP_N, rest, mm, bs, mk(-1, 0), L + (size_t)(k0 + bs) + (size_t)k0 * ldl,
+                                       ldl, Xb, ldx, mk(1, 0), Xb + bs, ldx), nullptr, 0)))
+            return rc;
       }
-    }
-  } else {
-    for (int b = nblk - 1; b >= 0; --b) {
-      const int k0 = b * DB, bs = std::min(DB, n - k0);
-      cplx* Xb = X + k0;
-      rc = zgemm(c, gemm_args(OP_C, OP_N, bs, m, bs, mk(1, 0), Linv + (size_t)b * DB * DB, DB, Xb, ldx,
-                                 mk(0, 0), Xb, ldx), nullptr, 0);
-      if (rc) return rc;
-      if (k0 > 0) {
-        // X[0:k0] -= L[k0:k0+bs, 0:k0]^H X_b
-        rc = zgemm(c, gemm_args(OP_C, OP_N, k0, m, bs, mk(-1, 0), L + k0, ldl, Xb, ldx, mk(1, 0), X, ldx),
-                   nullptr, 0);
-        if (rc) return rc;
+    } else {
+      for (int b = nblk - 1; b >= 0; --b) {
+        const int k0 = b * TB, bs = std::min(TB, n - k0);
+        cplx* Xb = Xc + k0;
+        if ((rc = zgemm(c, gemm_args(OP_C, OP_N, bs, mm, bs, mk(1, 0), Linv + (size_t)b * TB * TB, TB, Xb, ldx,
+                                     mk(0, 0), T, TB), nullptr, 0)))
+          return rc;
+        k_copy_block<<<1024, 256, 0, c.st>>>(T, TB, Xb, ldx, bs, mm);
+        count_launch();
+        if (k0 > 0)
+          if ((rc = zgemm(c, gemm_args(OP_C, OP_N, k0, mm, bs, mk(-1, 0), L + k0, ldl, Xb, ldx, mk(1, 0), Xc, ldx),
+                          nullptr, 0)))
+            return rc;
       }
     }
   }
