@@ -173,6 +173,29 @@ int gbhe_crt_workspace_size(int m, int n, int k, int cplx, size_t* bytes);
 int gbhe_gemm_crt(gbhe_handle h, int cplx, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const void* A,
                   int lda, const void* B, int ldb, gbhe_cplx beta, void* C, int ldc, int lower, void* stream);
 
+/* The complex DMMA GEMM of gbhe_zgemm (same operand modes and arguments, no
+ * handle) for callers that cannot allocate: code that must not take device
+ * memory after start-up, or that holds no handle and so has no workspace to
+ * hand over.  It allocates nothing.  Its split-K partial sums live in a
+ * statically sized array inside the library (GBHE_ZGEMM_STATIC_SCRATCH
+ * complex values, 16 MiB), which the CUDA module provides on load; no part of
+ * that array has to start at zero.
+ *   - m * n may be at most GBHE_ZGEMM_STATIC_MAX_MN; larger products return
+ *     GBHE_ETOOLARGE and leave C untouched.  k is not limited.
+ *   - The first call on each device (the device current at the call) looks up
+ *     the array's address on that device; make that first call before any
+ *     stream capture on the device.
+ *   - The array is shared by every call on a device: two calls whose work
+ *     overlaps in time (different streams, or different host threads) race on
+ *     it and give wrong results.  Calls issued in order on one stream are safe.
+ * Returns 0, a negative argument index, GBHE_ETOOLARGE or GBHE_ECUDA.  Not
+ * part of the paper's method: the paper has no counterpart. */
+#define GBHE_ETOOLARGE (-106)                   /* product larger than the static scratch allows */
+#define GBHE_ZGEMM_STATIC_SCRATCH (1 << 20)     /* complex128 values of split-K scratch */
+#define GBHE_ZGEMM_STATIC_MAX_MN (1 << 18)      /* largest m * n accepted */
+int gbhe_zgemm_static(int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const gbhe_cplx* A, int lda,
+                      const gbhe_cplx* B, int ldb, gbhe_cplx beta, gbhe_cplx* C, int ldc, int lower, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (host-side counter; benchmarks difference it around a timed region). */
 unsigned long long gbhe_launch_count(void);

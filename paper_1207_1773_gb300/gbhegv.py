@@ -75,6 +75,7 @@ def _load():
             "gbhe_profile_read": ([I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
             "gbhe_probe_fp64_peaks": ([I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
+            "gbhe_zgemm_static": ([I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -95,7 +96,7 @@ def exported_symbols():
                         "gbhe_trsm_lh", "gbhe_hegv", "gbhe_hegv_onestage", "gbhe_status_string",
                         "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
-                        "gbhe_set_gemm_engine")]
+                        "gbhe_set_gemm_engine", "gbhe_zgemm_static")]
 
 
 def status_string(code: int) -> str:
@@ -340,6 +341,21 @@ def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     _check("gbhe_zgemm", _load().gbhe_zgemm(h.h, OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag), _ptr(A),
                                             _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C), _ld(C),
                                             int(bool(lower)), _stream(C.device)))
+    return C
+
+
+def zgemm_static(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
+    """C = alpha op(A) op(B) + beta C on the DMMA GEMM with split-K scratch in
+    the library's static array (no handle, no workspace), in place.  Calls
+    must not overlap in time on one device; m * n <= 2**18."""
+    m, n = C.shape
+    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    a, b = complex(alpha), complex(beta)
+    with torch.cuda.device(C.device):
+        _check("gbhe_zgemm_static",
+               _load().gbhe_zgemm_static(OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag), _ptr(A), _ld(A),
+                                         _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C), _ld(C),
+                                         int(bool(lower)), _stream(C.device)))
     return C
 
 
