@@ -288,28 +288,33 @@ __device__ __forceinline__ void hmma(float (&c)[4], const unsigned (&a)[4], unsi
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float fmod_acc(float x, float p, float pinv) {
-  // x an integer-valued float with |x| <= 2^24; result in [0, p)
-  float q = floorf(x * pinv);
-  float r = fmaf(-q, p, x);
-  if (r < 0.f) r += p;
-  if (r >= p) r -= p;
-  return r;
-}
+// x - p rint(x / p) for an integer-valued x with |x| <= 2^24: an integer of
+// magnitude at most p/2 + 1, exact in FP32 (the FMA rounds nothing away).
+__device__ __forceinline__ float red_sym(float x, float p, float pinv) { return fmaf(-rintf(x * pinv), p, x); }
+
+// Residues of one output tile in the tile-major layout shared with the
+// reconstruction: tile t = by * TM + bx (TM = ceil(maxM / CBM)), and for
+// modulus l and component c a CBM x CBN byte block, column-major, at
+// Out + ((t * NMOD + l) * ncout + c) * CBM * CBN.
+constexpr int OTILE = CBM * CBN;
+constexpr int OPITCH = CBM + 16;  // smem column pitch of the staged tile (bank-spread, 16 B aligned)
 
 // grid (ceil(M/CBM), ceil(N/CBN), NMOD); 8 warps as 4 (M) x 2 (N), warp tile 32 x 32.
 // PA: residue planes of op(A) (R = M), PB: of op(B) (R = N); both K-padded to Kp.
-// Out: bytes [l][comp][j][i] (column-major per plane), comp = re (and im).
 // Batched form (D != nullptr): blockIdx.z = entry * NMOD + modulus; entry
 // regions of the planes and outputs are sized for maxM / maxN, the layout
-// inside an entry uses the entry's own M, N.
+// inside an entry's planes uses the entry's own M, N.  lower != 0 skips tiles
+// strictly above the diagonal (their outputs are never read).
 template <bool CPLX>
 __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __half* PB, int M, int N, int Kp,
-                                                   unsigned char* Out, const CrtDesc* D, int maxM, int maxN) {
+                                                   unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
+                                                   int lower) {
   constexpr int NC = CPLX ? 3 : 1;
+  constexpr int NCOUT = CPLX ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __half* sm = reinterpret_cast<__half*>(smem_raw);
   constexpr int A_ST = NC * CBM * KPAD, B_ST = NC * CBN * KPAD, ST = A_ST + B_ST;
+  const int TM = (maxM + CBM - 1) / CBM, TN = (maxN + CBN - 1) / CBN;
   int l = blockIdx.z;
   if (D) {
     const int entry = blockIdx.z / NMOD;
@@ -318,10 +323,11 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
     N = D[entry].N;
     PA += (size_t)entry * NMOD * NC * maxM * Kp;
     PB += (size_t)entry * NMOD * NC * maxN * Kp;
-    Out += (size_t)entry * NMOD * (CPLX ? 2 : 1) * maxM * maxN;
+    Out += (size_t)entry * TM * TN * NMOD * NCOUT * OTILE;
   }
   const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
   if (m0 >= M || n0 >= N) return;
+  if (lower && m0 + CBM - 1 < n0) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int wm = (w & 3) * 32, wn = (w >> 2) * 32;
   const float p = (float)c_p[l], pinv = c_pinv[l];
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
   const __half* Bl = PB + (size_t)l * NC * planeB;
 
   float acc[NC][2][4][4];
-  float res[CPLX ? 2 : 1][2][4][4];
+  float res[NCOUT][2][4][4];
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[c][a][b][q] = 0.f;
 #pragma unroll
-  for (int c = 0; c < (CPLX ? 2 : 1); ++c)
+  for (int c = 0; c < NCOUT; ++c)
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -366,6 +372,9 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
     }
   };
 
+  // Fold one exact chunk into the running residues.  The running sums are
+  // kept as unreduced integers (each chunk adds at most 2p + 2 in magnitude,
+  // and K <= 2^16 gives at most 128 chunks), reduced once at the end.
   auto flush = [&]() {
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -375,19 +384,11 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
         for (int q = 0; q < 4; ++q) {
           if (CPLX) {
             const float p1 = acc[0][a][b][q], p2 = acc[1][a][b][q], p3 = acc[2][a][b][q];
-            // |p| <= 2^23: differences stay exact in fp32
-            float cr = fmod_acc(p1 - p2, p, pinv);
-            float ci = fmod_acc(fmod_acc(p3, p, pinv) - fmod_acc(p1 + p2, p, pinv), p, pinv);
-            float sr = res[0][a][b][q] + cr;
-            float si = res[CPLX ? 1 : 0][a][b][q] + ci;
-            if (sr >= p) sr -= p;
-            if (si >= p) si -= p;
-            res[0][a][b][q] = sr;
-            res[CPLX ? 1 : 0][a][b][q] = si;
+            // |p_i| <= 2^23, so p1 - p2 and p1 + p2 are exact
+            res[0][a][b][q] += red_sym(p1 - p2, p, pinv);
+            res[NCOUT - 1][a][b][q] += red_sym(p3, p, pinv) - red_sym(p1 + p2, p, pinv);
           } else {
-            float s = res[0][a][b][q] + fmod_acc(acc[0][a][b][q], p, pinv);
-            if (s >= p) s -= p;
-            res[0][a][b][q] = s;
+            res[0][a][b][q] += red_sym(acc[0][a][b][q], p, pinv);
           }
 #pragma unroll
           for (int c = 0; c < NC; ++c) acc[c][a][b][q] = 0.f;
@@ -400,7 +401,6 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
     if (s < ktiles) load(s, s * CBK);
     cp_commit();
   }
-  const int gq = lane >> 2, tq = lane & 3;
   for (int kt = 0; kt < ktiles; ++kt) {
     cp_wait<CSTAGE - 2>();
     __syncthreads();
@@ -441,21 +441,35 @@ __global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __ha
   }
   cp_wait<0>();
   if ((ktiles * CBK) % KC != 0) flush();
-  (void)gq; (void)tq;
-  // store residues: element (row, col) of the 16x8 C fragment q: row = g + 8*(q>>1), col = 2*tq + (q&1)
-  const int ncout = CPLX ? 2 : 1;
+  __syncthreads();  // every warp is done with the operand stages: reuse them for the output tile
+  // Reduce to [0, p) and stage the bytes column-major in shared memory.  Element
+  // q of the 16x8 fragment: row g + 8 (q >> 1), column 2 tq + (q & 1).
+  unsigned char* stile = smem_raw;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int i = m0 + wm + a * 16 + (lane >> 2) + 8 * (q >> 1);
-        const int j = n0 + wn + b * 8 + 2 * (lane & 3) + (q & 1);
-        if (i >= M || j >= N) continue;
-        for (int c = 0; c < ncout; ++c)
-          Out[((size_t)(l * ncout + c) * N + j) * M + i] = (unsigned char)res[c][a][b][q];
+        const int il = wm + a * 16 + (lane >> 2) + 8 * (q >> 1);
+        const int jl = wn + b * 8 + 2 * (lane & 3) + (q & 1);
+#pragma unroll
+        for (int c = 0; c < NCOUT; ++c) {
+          float v = red_sym(res[c][a][b][q], p, pinv);
+          if (v < 0.f) v += p;
+          if (v >= p) v -= p;
+          stile[(c * CBN + jl) * OPITCH + il] = (unsigned char)(int)v;
+        }
       }
+  __syncthreads();
+  unsigned char* dst = Out + ((size_t)(blockIdx.y * TM + blockIdx.x) * NMOD + l) * NCOUT * OTILE;
+  // only the 16-row chunks and columns that hold outputs (the rest is never read)
+  const int nu = (min(CBM, M - m0) + 15) / 16, ncol = min(CBN, N - n0);
+  for (int i = t; i < NCOUT * ncol * nu; i += CNT) {
+    const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, u = rem % nu;
+    const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * CBN + jl) * OPITCH + u * 16);
+    *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + jl) * CBM + u * 16) = v;
+  }
 }
 
 // ------------------------------------------------------------------ reconstruction
@@ -485,15 +499,21 @@ __device__ __forceinline__ double int160_to_double(unsigned (&D)[5], int sc) {
       c = (c && D[i] == 0) ? 1 : 0;
     }
   }
-  int top = 4;
-  while (top > 0 && D[top] == 0) --top;
-  if (D[top] == 0) return 0.0;
+  // the leading nonzero word (t2), the two below it and a sticky bit for the rest,
+  // chosen by comparisons so that D stays in registers
+  int top;
+  unsigned t2, t1, t0;
+  bool sticky;
+  if (D[4]) { top = 4; t2 = D[4]; t1 = D[3]; t0 = D[2]; sticky = (D[1] | D[0]) != 0; }
+  else if (D[3]) { top = 3; t2 = D[3]; t1 = D[2]; t0 = D[1]; sticky = D[0] != 0; }
+  else if (D[2]) { top = 2; t2 = D[2]; t1 = D[1]; t0 = D[0]; sticky = false; }
+  else if (D[1]) { top = 1; t2 = D[1]; t1 = D[0]; t0 = 0; sticky = false; }
+  else if (D[0]) { top = 0; t2 = D[0]; t1 = 0; t0 = 0; sticky = false; }
+  else return 0.0;
   // take 64 bits starting at the top word
-  const int lz = __clz(D[top]);
-  unsigned long long hi = ((unsigned long long)D[top] << 32) | (top >= 1 ? D[top - 1] : 0u);
-  unsigned long long lo = top >= 2 ? ((unsigned long long)D[top - 2] << 32) : 0ull;
-  bool sticky = false;
-  for (int i = top - 3; i >= 0; --i) sticky |= (D[i] != 0);
+  const int lz = __clz(t2);
+  unsigned long long hi = ((unsigned long long)t2 << 32) | t1;
+  unsigned long long lo = (unsigned long long)t0 << 32;
   // normalise: shift left by lz so bit 63 of hi is set
   if (lz) { hi = (hi << lz) | (lo >> (64 - lz)); lo <<= lz; }
   sticky |= (lo != 0);
@@ -516,31 +536,50 @@ __device__ __forceinline__ double int160_to_double(unsigned (&D)[5], int sc) {
   return __longlong_as_double((long long)bits);
 }
 
-__device__ __forceinline__ double crt_value(const unsigned char* R, size_t stride, int sc) {
+// CRT value of residue byte `sh / 8` of every word w[l] (one word per modulus).
+// The tables (W_l, y_l / p_l, M) of the reconstruction, copied to shared memory
+// by each block and read through a volatile pointer at every use, so that the
+// compiler does not keep all of them in registers across the element loop.
+struct CrtTables {
+  unsigned W[NMOD][4];
+  float frac[NMOD];
+  unsigned M[4];
+};
+
+__device__ __forceinline__ const volatile CrtTables* load_tables() {
+  __shared__ CrtTables tb;
+  for (int i = threadIdx.x; i < NMOD * 4; i += blockDim.x) tb.W[i / 4][i % 4] = c_W[i / 4][i % 4];
+  for (int i = threadIdx.x; i < NMOD; i += blockDim.x) tb.frac[i] = c_frac[i];
+  if (threadIdx.x < 4) tb.M[threadIdx.x] = c_M[threadIdx.x];
+  __syncthreads();
+  return &tb;
+}
+
+__device__ __forceinline__ double crt_value(const volatile CrtTables* tb, const unsigned (&w)[NMOD], int sh, int sc) {
   unsigned S[5] = {0, 0, 0, 0, 0};
   float F = 0.f;
 #pragma unroll
   for (int l = 0; l < NMOD; ++l) {
-    const unsigned c = R[(size_t)l * stride];
-    const unsigned W[4] = {c_W[l][0], c_W[l][1], c_W[l][2], c_W[l][3]};
+    const unsigned c = (w[l] >> sh) & 0xFFu;
+    const unsigned W[4] = {tb->W[l][0], tb->W[l][1], tb->W[l][2], tb->W[l][3]};
     mac160(S, c, W);
-    F = fmaf((float)c, c_frac[l], F);
+    F = fmaf((float)c, tb->frac[l], F);
   }
   const unsigned q = (unsigned)rintf(F);
   // D = S - q M
   unsigned qM[5] = {0, 0, 0, 0, 0};
-  const unsigned Mw[4] = {c_M[0], c_M[1], c_M[2], c_M[3]};
+  const unsigned Mw[4] = {tb->M[0], tb->M[1], tb->M[2], tb->M[3]};
   mac160(qM, q & 0xFFu, Mw);
   if (q >> 8) {  // q < 2^12
     unsigned t2[5] = {0, 0, 0, 0, 0};
     mac160(t2, q >> 8, Mw);
     // qM += t2 << 8
     unsigned carry = 0;
-    unsigned sh[5];
-    sh[0] = t2[0] << 8;
-    for (int i = 1; i < 5; ++i) sh[i] = (t2[i] << 8) | (t2[i - 1] >> 24);
+    unsigned sh8[5];
+    sh8[0] = t2[0] << 8;
+    for (int i = 1; i < 5; ++i) sh8[i] = (t2[i] << 8) | (t2[i - 1] >> 24);
     for (int i = 0; i < 5; ++i) {
-      unsigned long long s = (unsigned long long)qM[i] + sh[i] + carry;
+      unsigned long long s = (unsigned long long)qM[i] + sh8[i] + carry;
       qM[i] = (unsigned)s;
       carry = (unsigned)(s >> 32);
     }
@@ -555,76 +594,58 @@ __device__ __forceinline__ double crt_value(const unsigned char* R, size_t strid
   return int160_to_double(D, sc);
 }
 
-// C = alpha * (A B) + beta * C from the residues; one thread per element.
-__global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const int* ea, const int* eb, GemmArgs g,
-                                  int cplx) {
-  const size_t total = (size_t)M * N;
-  const int ncout = cplx ? 2 : 1;
-  const size_t stride = (size_t)ncout * total;
-  const bool beta0 = (g.beta.x == 0.0 && g.beta.y == 0.0);
-  const bool beta1 = (g.beta.x == 1.0 && g.beta.y == 0.0);
-  const bool alpha1 = (g.alpha.x == 1.0 && g.alpha.y == 0.0);
-  const bool alpham1 = (g.alpha.x == -1.0 && g.alpha.y == 0.0);
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % M), j = (int)(idx / M);
-    if (g.lower_only && i < j) continue;
-    const int sc = ea[i] + eb[j] - 104;
-    double vr = crt_value(Out + idx, stride, sc);
-    double vi = cplx ? crt_value(Out + total + idx, stride, sc) : 0.0;
-    double2 out;
-    if (alpha1) out = make_double2(vr, vi);
-    else if (alpham1) out = make_double2(-vr, -vi);
-    else out = cmul(g.alpha, make_double2(vr, vi));
-    const size_t ci = (size_t)i + (size_t)j * g.ldc;
-    if (cplx) {
-      double2* C = reinterpret_cast<double2*>(g.C);
-      if (beta1) out = cadd(out, C[ci]);
-      else if (!beta0) out = cadd(out, cmul(g.beta, C[ci]));
-      C[ci] = out;
-    } else {
-      double* C = reinterpret_cast<double*>(g.C);
-      double o = out.x;
-      if (beta1) o += C[ci];
-      else if (!beta0) o += g.beta.x * C[ci];
-      C[ci] = o;
-    }
-  }
-}
-
-// Batched reconstruction: C_z = alpha (A_z B_z) + beta C_z for every entry z.
-__global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, int nbatch, int maxM, int maxN,
-                                   const int* ea, const int* eb, double2 alpha, double2 beta, int cplx) {
-  const size_t per = (size_t)maxM * maxN;
-  const size_t total = per * nbatch;
+// Reconstruct four consecutive rows i0..i0+3 of column j of one output tile
+// (tile base `T` in the tile-major residue layout, offset `loc` inside it)
+// and update C.
+__device__ __forceinline__ void crt_store4(const volatile CrtTables* tb, const unsigned char* T, int loc, int i0,
+                                           int j, int M, int lower,
+                                           const int* ea, int ebj, double2 alpha, double2 beta, int cplx, void* Cv,
+                                           int ldc) {
   const int ncout = cplx ? 2 : 1;
   const bool beta0 = (beta.x == 0.0 && beta.y == 0.0);
   const bool beta1 = (beta.x == 1.0 && beta.y == 0.0);
   const bool alpha1 = (alpha.x == 1.0 && alpha.y == 0.0);
   const bool alpham1 = (alpha.x == -1.0 && alpha.y == 0.0);
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-    const int z = (int)(q / per);
-    const size_t r = q % per;
-    const CrtDesc d = D[z];
-    const int i = (int)(r % maxM), j = (int)(r / maxM);
-    if (i >= d.M || j >= d.N) continue;
-    const size_t tot = (size_t)d.M * d.N, idx = (size_t)i + (size_t)j * d.M;
-    const unsigned char* O = Out + (size_t)z * NMOD * ncout * per;
-    const int sc = ea[(size_t)z * maxM + i] + eb[(size_t)z * maxN + j] - 104;
-    const double vr = crt_value(O + idx, (size_t)ncout * tot, sc);
-    const double vi = cplx ? crt_value(O + tot + idx, (size_t)ncout * tot, sc) : 0.0;
+  // real parts of the four rows, then imaginary parts: one set of residue
+  // words live at a time
+  double vr[4], vi[4];
+  int sc[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) sc[r] = (i0 + r < M) ? ea[i0 + r] + ebj - 104 : 0;
+  {
+    unsigned w[NMOD];
+#pragma unroll
+    for (int l = 0; l < NMOD; ++l) w[l] = *reinterpret_cast<const unsigned*>(T + (size_t)(l * ncout) * OTILE + loc);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) vr[r] = crt_value(tb, w, 8 * r, sc[r]);
+  }
+  if (cplx) {
+    unsigned w[NMOD];
+#pragma unroll
+    for (int l = 0; l < NMOD; ++l)
+      w[l] = *reinterpret_cast<const unsigned*>(T + (size_t)(l * ncout + 1) * OTILE + loc);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) vi[r] = crt_value(tb, w, 8 * r, sc[r]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) vi[r] = 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + r;
+    if (i >= M || (lower && i < j)) continue;
     double2 out;
-    if (alpha1) out = make_double2(vr, vi);
-    else if (alpham1) out = make_double2(-vr, -vi);
-    else out = cmul(alpha, make_double2(vr, vi));
-    const size_t ci = (size_t)i + (size_t)j * d.ldc;
+    if (alpha1) out = make_double2(vr[r], vi[r]);
+    else if (alpham1) out = make_double2(-vr[r], -vi[r]);
+    else out = cmul(alpha, make_double2(vr[r], vi[r]));
+    const size_t ci = (size_t)i + (size_t)j * ldc;
     if (cplx) {
-      double2* C = reinterpret_cast<double2*>(d.C);
+      double2* C = reinterpret_cast<double2*>(Cv);
       if (beta1) out = cadd(out, C[ci]);
       else if (!beta0) out = cadd(out, cmul(beta, C[ci]));
       C[ci] = out;
     } else {
-      double* C = reinterpret_cast<double*>(d.C);
+      double* C = reinterpret_cast<double*>(Cv);
       double o = out.x;
       if (beta1) o += C[ci];
       else if (!beta0) o += beta.x * C[ci];
@@ -633,13 +654,64 @@ __global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, i
   }
 }
 
+// C = alpha * (A B) + beta * C from the residues; one thread per four
+// consecutive rows of a tile column (4-byte loads of every residue block).
+__global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const int* ea, const int* eb, GemmArgs g,
+                                  int cplx) {
+  const volatile CrtTables* tb = load_tables();
+  const int TM = (M + CBM - 1) / CBM, TN = (N + CBN - 1) / CBN;
+  const int ncout = cplx ? 2 : 1;
+  const size_t per_tile = OTILE / 4;
+  const size_t groups = (size_t)TM * TN * per_tile;
+  for (size_t gi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; gi < groups;
+       gi += (size_t)gridDim.x * blockDim.x) {
+    const size_t tile = gi / per_tile;
+    const int loc = (int)(gi % per_tile) * 4;
+    const int bx = (int)(tile % TM), by = (int)(tile / TM);
+    const int i0 = bx * CBM + loc % CBM, j = by * CBN + loc / CBM;
+    if (i0 >= M || j >= N) continue;
+    if (g.lower_only && i0 + 3 < j) continue;
+    crt_store4(tb, Out + tile * NMOD * ncout * OTILE, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, cplx,
+               g.C, g.ldc);
+  }
+}
+
+// Batched reconstruction: C_z = alpha (A_z B_z) + beta C_z for every entry z
+// (tiles laid out for maxM x maxN per entry).
+__global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, int nbatch, int maxM, int maxN,
+                                   const int* ea, const int* eb, double2 alpha, double2 beta, int cplx) {
+  const volatile CrtTables* tb = load_tables();
+  const int TM = (maxM + CBM - 1) / CBM, TN = (maxN + CBN - 1) / CBN;
+  const int ncout = cplx ? 2 : 1;
+  const size_t per_tile = OTILE / 4;
+  const size_t tiles = (size_t)TM * TN;
+  const size_t groups = (size_t)nbatch * tiles * per_tile;
+  for (size_t gi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; gi < groups;
+       gi += (size_t)gridDim.x * blockDim.x) {
+    const size_t tile = gi / per_tile;  // global tile index over entries
+    const int z = (int)(tile / tiles);
+    const size_t tz = tile % tiles;
+    const int loc = (int)(gi % per_tile) * 4;
+    const int bx = (int)(tz % TM), by = (int)(tz / TM);
+    const int i0 = bx * CBM + loc % CBM, j = by * CBN + loc / CBM;
+    const CrtDesc d = D[z];
+    if (i0 >= d.M || j >= d.N) continue;
+    crt_store4(tb, Out + tile * NMOD * ncout * OTILE, loc, i0, j, d.M, 0, ea + (size_t)z * maxM,
+               eb[(size_t)z * maxN + j], alpha, beta, cplx, d.C, d.ldc);
+  }
+}
+
+inline size_t out_bytes(int M, int N, int cplx) {
+  return (size_t)((M + CBM - 1) / CBM) * ((N + CBN - 1) / CBN) * NMOD * (cplx ? 2 : 1) * OTILE;
+}
+
 size_t crt_bytes(int M, int N, int K, int cplx) {
   const size_t Kp = (size_t)(K + CBK - 1) / CBK * CBK;
   const int nc = cplx ? 3 : 1;
   size_t b = 0;
   b += (size_t)NMOD * nc * (size_t)M * Kp * 2 + 256;
   b += (size_t)NMOD * nc * (size_t)N * Kp * 2 + 256;
-  b += (size_t)NMOD * (cplx ? 2 : 1) * (size_t)M * N + 256;
+  b += out_bytes(M, N, cplx) + 256;
   b += ((size_t)M + N) * sizeof(int) + 512;
   return b;
 }
@@ -663,7 +735,7 @@ size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) 
   size_t b = 0;
   b += nbt * NMOD * nc * (size_t)maxM * Kp * 2 + 256;
   b += nbt * NMOD * nc * (size_t)maxN * Kp * 2 + 256;
-  b += nbt * NMOD * (cplx ? 2 : 1) * (size_t)maxM * maxN + 256;
+  b += nbt * out_bytes(maxM, maxN, cplx) + 256;
   b += nbt * ((size_t)maxM + maxN) * sizeof(int) + 512;
   return b;
 }
@@ -681,7 +753,7 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
   __half* PA = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxM * Kp * 2));
   __half* PB = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxN * Kp * 2));
-  unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)nbatch * NMOD * (cplx_flag ? 2 : 1) * maxM * maxN));
+  unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)nbatch * out_bytes(maxM, maxN, cplx_flag)));
   int* ea = reinterpret_cast<int*>(take((size_t)nbatch * maxM * sizeof(int)));
   int* eb = reinterpret_cast<int*>(take((size_t)nbatch * maxN * sizeof(int)));
   ProfScope prof(st, GBHE_PROF_CRT, 0.0, 0.0);
@@ -705,16 +777,16 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_c = true;
     }
-    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN);
+    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0);
   } else {
     if (!attr_r) {
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_r = true;
     }
-    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN);
+    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0);
   }
   count_launch();
-  const size_t total = (size_t)nbatch * maxM * maxN;
+  const size_t total = (size_t)nbatch * out_bytes(maxM, maxN, 0) / NMOD / 4;  // four outputs per thread
   k_bcrt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, D, nbatch, maxM, maxN,
                                                                                            ea, eb, alpha, beta,
                                                                                            cplx_flag);
@@ -724,7 +796,9 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
 
 size_t crt_budget_bytes(int n) {
   const int b = std::max(1, std::min(n, CRT_BLOCK));
-  return crt_bytes(b, b, b, 1);
+  // at least 64 MiB: the batched products of small problems (one padded
+  // 128 x 64 output tile per entry) need more than an n x n x n product
+  return std::max(crt_bytes(b, b, b, 1), size_t(64) << 20);
 }
 
 int gemm(Ctx& c, const GemmArgs& g, int cplx) {
@@ -795,7 +869,7 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
   __half* PA = reinterpret_cast<__half*>(take((size_t)NMOD * nc * M * Kp * 2));
   __half* PB = reinterpret_cast<__half*>(take((size_t)NMOD * nc * N * Kp * 2));
-  unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)NMOD * (cplx ? 2 : 1) * M * N));
+  unsigned char* Out = reinterpret_cast<unsigned char*>(take(out_bytes(M, N, cplx)));
   int* ea = reinterpret_cast<int*>(take((size_t)M * sizeof(int)));
   int* eb = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
   const Operand oa = make_operand(g.A, g.lda, M, K, g.opA, true, cplx);
@@ -822,16 +896,16 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_c = true;
     }
-    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, 0, 0);
+    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only);
   } else {
     if (!attr_r) {
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_r = true;
     }
-    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, 0, 0);
+    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only);
   }
   count_launch();
-  const size_t total = (size_t)M * N;
+  const size_t total = out_bytes(M, N, 0) / NMOD / 4;  // four outputs per thread
   k_crt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, M, N, ea, eb, g, cplx);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
