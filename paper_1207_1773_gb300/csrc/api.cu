@@ -421,7 +421,7 @@ int gbhe_gemm_crt(gbhe_handle h, int cplx, int opA, int opB, int m, int n, int k
   const size_t need = crt_gemm_ws_bytes(m, n, k, cplx ? 1 : 0);
   char* ws = c.arena.take<char>(need);
   if (!c.arena.ok() || !ws) return GBHE_EWORKSPACE;
-  return crt_gemm(c.st, g, cplx ? 1 : 0, ws, need);
+  return crt_gemm(c.st, g, cplx ? 1 : 0, ws, need, c.status);
 }
 
 }  // extern "C"

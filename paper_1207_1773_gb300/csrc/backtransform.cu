@@ -282,10 +282,10 @@ static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const c
       k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, t, b_lo, cnt, Vg, Ug, X, ldx, c0, mcc, Wbuf, D1, D2);
       count_launch();
       rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, nb, mcc, W2 - 1, c.crt_ws,
-                            c.crt_ws_bytes);
+                            c.crt_ws_bytes, c.status);
       if (!rc)
         rc = crt_gemm_batched(c.st, OP_N, OP_N, mk(-1, 0), mk(1, 0), 1, D2, cnt, W2 - 1, mcc, nb, c.crt_ws,
-                              c.crt_ws_bytes);
+                              c.crt_ws_bytes, c.status);
     }
   }
   ar.off = save;

@@ -10,14 +10,16 @@
 //      the level of the last bit of the largest element of the row/column).
 //   2. Residues.  The integers are reduced modulo NMOD = 16 pairwise coprime
 //      moduli p_l <= 256 (product M ~ 2^125) to symmetric residues |r| <= 128,
-//      exact in FP16.  Complex operands give three planes per modulus:
-//      Re, Im and Re + Im (Karatsuba, exact in modular arithmetic).
-//   3. Products.  For each modulus the three residue products
-//      P1 = Ar Br, P2 = Ai Bi, P3 = (Ar + Ai)(Br + Bi) run on mma.sync
-//      m16n8k16 f16 -> f32.  Every partial sum of at most KC = 512 products
-//      of |r| <= 128 stays below 2^23, so the FP32 accumulation is exact;
-//      after each chunk the sums are reduced mod p_l.  Re C = P1 - P2,
-//      Im C = P3 - P1 - P2 (mod p_l) are stored as bytes.
+//      exact in FP16.  Complex operands give two planes (Re, Im) per modulus.
+//   3. Products.  For each modulus the residue products run on tcgen05.mma
+//      kind::f16 (f16 -> f32 accumulators in tensor memory): real operands
+//      one product, complex operands Re C = Ar Br - Ai Bi and
+//      Im C = Ar Bi + Ai Br (the subtraction by the MMA's negate-A bit).
+//      Every partial sum of at most 2^23 / 128^2 = 512 products of
+//      |r| <= 128 (chunks of 512 contraction terms real, 256 complex, which add
+//      two products per term) is an integer below 2^23, so the FP32
+//      accumulation is exact; after each chunk the sums are reduced mod p_l
+//      and the residues of Re C and Im C are stored as bytes.
 //   4. Reconstruction.  C_int = sum_l c_l W_l - q M (CRT, W_l = M_l (M_l^-1
 //      mod p_l)) in 160-bit integer arithmetic, q = round(sum_l c_l y_l/p_l)
 //      (the true value is far inside (-M/2, M/2): |C_int| <= K 2^105 < M/8
@@ -36,9 +38,7 @@ namespace gbhe {
 namespace {
 
 constexpr int NMOD = 16;
-constexpr int KC = 512;              // exact FP32 chunk length
-constexpr int CBM = 128, CBN = 64, CBK = 32, CNT = 256, CSTAGE = 3;
-constexpr int KPAD = CBK + 8;        // smem row pitch in halfs (80 B: ldmatrix conflict-free)
+constexpr int CBM = 128, CBN = 64, CBK = 32;  // output tile of the residue products; K padding
 constexpr int KMAX = 65536;          // contraction bound of the margin argument above
 
 const int h_mod[NMOD] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 211, 199, 197, 193, 191};
@@ -180,7 +180,7 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
     if (r_contig) tile[tx][q] = v; else tile[q][tx] = v;
   }
   __syncthreads();
-  const int ncomp = o.cplx ? 3 : 1;
+  const int ncomp = o.cplx ? 2 : 1;
   const size_t plane = (size_t)o.R * Kp;
   for (int q = ty; q < 32; q += 8) {
     const int r = r0 + q, k = k0 + tx;  // k contiguous in the output
@@ -222,11 +222,7 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
       dst[0] = __float2half_rn(s0);
       if (o.cplx) {
         float s1 = rr[1] > half_p ? rr[1] - p : rr[1];
-        float ss = rr[0] + rr[1];
-        if (ss >= p) ss -= p;
-        ss = ss > half_p ? ss - p : ss;
         dst[plane] = __float2half_rn(s1);
-        dst[2 * plane] = __float2half_rn(ss);
       }
     }
   }
@@ -259,7 +255,7 @@ __global__ void k_bop_exponents(const CrtDesc* D, int isA, int op, int cplx, int
 __global__ void k_bop_residues(const CrtDesc* D, int isA, int op, int cplx, int maxR, const int* e, int Kp,
                                __half* P) {
   const Operand o = desc_operand(D[blockIdx.z], isA, op, cplx);
-  const size_t entry = (size_t)NMOD * (cplx ? 3 : 1) * maxR * Kp;
+  const size_t entry = (size_t)NMOD * (cplx ? 2 : 1) * maxR * Kp;
   op_residues_tile(o, e + (size_t)blockIdx.z * maxR, Kp, P + blockIdx.z * entry, blockIdx.x, blockIdx.y);
 }
 
@@ -276,18 +272,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
-}
-
-__device__ __forceinline__ void hmma(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // x - p rint(x / p) for an integer-valued x with |x| <= 2^24: an integer of
 // magnitude at most p/2 + 1, exact in FP32 (the FMA rounds nothing away).
 __device__ __forceinline__ float red_sym(float x, float p, float pinv) { return fmaf(-rintf(x * pinv), p, x); }
@@ -299,177 +283,287 @@ __device__ __forceinline__ float red_sym(float x, float p, float pinv) { return 
 constexpr int OTILE = CBM * CBN;
 constexpr int OPITCH = CBM + 16;  // smem column pitch of the staged tile (bank-spread, 16 B aligned)
 
-// grid (ceil(M/CBM), ceil(N/CBN), NMOD); 8 warps as 4 (M) x 2 (N), warp tile 32 x 32.
-// PA: residue planes of op(A) (R = M), PB: of op(B) (R = N); both K-padded to Kp.
-// Batched form (D != nullptr): blockIdx.z = entry * NMOD + modulus; entry
-// regions of the planes and outputs are sized for maxM / maxN, the layout
-// inside an entry's planes uses the entry's own M, N.  lower != 0 skips tiles
-// strictly above the diagonal (their outputs are never read).
+// ------------------------------------------------------------------ residue products on tcgen05
+// tcgen05.mma kind::f16 (FP16 operands from shared memory, FP32 accumulators
+// in tensor memory), issued by one thread; operands staged by cp.async in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// K-adjacent core matrices 128 B apart, 8-row groups 512 B apart).
+//
+// One CTA computes a UBM x UBN output tile for `mpc` consecutive moduli.  Its
+// work is a flat sequence of K tiles over those moduli, cut into units (one
+// exact chunk of one modulus).  Each unit accumulates Re and Im (one
+// accumulator for real operands) in one of two TMEM buffers; while the
+// tensor cores run unit u, the threads fold unit u - 1 into the running
+// residues and, at the end of a modulus, write its bytes in the tile-major
+// layout read by the reconstruction (two CBN-wide tiles per CTA).
+constexpr int UBM = 128, UBN = 128, UBK = 32;
+constexpr int UTHREADS = 256;
+constexpr int U_APL = UBM * UBK * 2, U_BPL = UBN * UBK * 2;  // bytes of one plane tile
+static_assert(UBM == CBM && UBN == 2 * CBN, "a CTA covers two tiles of the residue layout");
 template <bool CPLX>
-__global__ void __launch_bounds__(CNT, 1) k_crt_mma(const __half* PA, const __half* PB, int M, int N, int Kp,
-                                                   unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
-                                                   int lower) {
-  constexpr int NC = CPLX ? 3 : 1;
-  constexpr int NCOUT = CPLX ? 2 : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __half* sm = reinterpret_cast<__half*>(smem_raw);
-  constexpr int A_ST = NC * CBM * KPAD, B_ST = NC * CBN * KPAD, ST = A_ST + B_ST;
-  const int TM = (maxM + CBM - 1) / CBM, TN = (maxN + CBN - 1) / CBN;
-  int l = blockIdx.z;
+struct UCfg {
+  static constexpr int NC = CPLX ? 2 : 1;         // planes per operand = accumulators
+  static constexpr int STAGES = CPLX ? 5 : 6;
+  static constexpr int KC_TERMS = CPLX ? 256 : 512;  // exact chunk (contraction terms)
+  static constexpr unsigned BUFC = NC * UBN;         // TMEM columns of one buffer
+  static constexpr unsigned COLS = CPLX ? 512 : 256; // allocation (two buffers)
+  static constexpr int STB = NC * (U_APL + U_BPL);   // bytes per pipeline stage
+  static constexpr size_t SMEM = (size_t)STAGES * STB + (size_t)NC * UBN * OPITCH + 8 * (STAGES + 2) + 16;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
+// byte offsets between core matrices, descriptor version 1, no swizzle
+__device__ __forceinline__ unsigned long long umma_sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+  unsigned long long d = (unsigned long long)((addr & 0x3FFFFu) >> 4);
+  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+
+__device__ __forceinline__ void umma_f16(unsigned tmem_d, unsigned long long da, unsigned long long db, unsigned idesc,
+                                         unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Wait until the phase of parity `parity` of the mbarrier has completed, for
+// at most GBHE_WAIT_NS of %globaltimer; false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > GBHE_WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned addr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+#pragma unroll
+  for (int x = 0; x < 16; ++x) v[x] = __uint_as_float(r[x]);
+}
+
+// grid (TM * TN2 tiles in grouped order, 1, (NMOD/mpc) * nbatch), 256 threads;
+// TM = ceil(maxM/UBM), TN2 = ceil(maxN/UBN).  PA: residue planes of op(A)
+// (R = M), PB: of op(B) (R = N); both K-padded to Kp.  Batched form
+// (D != nullptr): blockIdx.z / (NMOD/mpc) is the entry; entry regions of the
+// planes and outputs are sized for maxM / maxN, the layout inside an entry's
+// planes uses the entry's own M, N.  lower != 0 skips tiles strictly above the
+// diagonal (their outputs are never read).  Timeouts of the bounded waits
+// record GBHE_ETIMEOUT in status[ST_ERR].
+template <bool CPLX>
+__global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, const __half* PB, int M, int N, int Kp,
+                                                         unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
+                                                         int lower, int mpc, int* status) {
+  using CF = UCfg<CPLX>;
+  constexpr int NC = CF::NC;
+  constexpr int STAGES = CF::STAGES;
+  constexpr int STB = CF::STB;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* stile = smem_raw + STAGES * STB;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile + NC * UBN * OPITCH);
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + STAGES + 2);
+  volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
+  const int TN = (maxN + CBN - 1) / CBN;  // tiles of the residue layout
+  const int ngrp = NMOD / mpc;
+  const int entry = blockIdx.z / ngrp, grp = blockIdx.z % ngrp;
+  // grouped order: eight tile rows at a time, so that concurrent CTAs share operand tiles in L2
+  int bx, by;
+  {
+    const int pid = blockIdx.x, GM = 8;
+    const int first = (pid / (GM * TN2)) * GM, gm = min(TM - first, GM);
+    bx = first + (pid % (GM * TN2)) % gm;
+    by = (pid % (GM * TN2)) / gm;
+  }
   if (D) {
-    const int entry = blockIdx.z / NMOD;
-    l = blockIdx.z % NMOD;
     M = D[entry].M;
     N = D[entry].N;
     PA += (size_t)entry * NMOD * NC * maxM * Kp;
     PB += (size_t)entry * NMOD * NC * maxN * Kp;
-    Out += (size_t)entry * TM * TN * NMOD * NCOUT * OTILE;
+    Out += (size_t)entry * TM * TN * NMOD * NC * OTILE;
   }
-  const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
+  const int m0 = bx * UBM, n0 = by * UBN;
   if (m0 >= M || n0 >= N) return;
-  if (lower && m0 + CBM - 1 < n0) return;
+  if (lower && m0 + UBM - 1 < n0) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int wm = (w & 3) * 32, wn = (w >> 2) * 32;
-  const float p = (float)c_p[l], pinv = c_pinv[l];
+  const int q = w & 3, h = w >> 2;  // TMEM lane quarter and column half of this warp
+  const int l0 = grp * mpc;
   const size_t planeA = (size_t)M * Kp, planeB = (size_t)N * Kp;
-  const __half* Al = PA + (size_t)l * NC * planeA;
-  const __half* Bl = PB + (size_t)l * NC * planeB;
 
-  float acc[NC][2][4][4];
-  float res[NCOUT][2][4][4];
+  if (t == 0) {
+    for (int i = 0; i < STAGES + 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *sabort = 0;
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(CF::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tslot;
+
+  const int ktiles = Kp / UBK;
+  constexpr int KTC = CF::KC_TERMS / UBK;  // K tiles per exact chunk
+  const int nch = (ktiles + KTC - 1) / KTC;
+  const int iters = mpc * ktiles;
+  // instruction descriptor: f32 accumulator, f16 A and B, both K-major, N, M
+  const unsigned idesc = (1u << 4) | ((unsigned)(UBN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
+  const unsigned idesc_negA = idesc | (1u << 13);
+
+  auto load = [&](int it) {
+    unsigned char* sA = smem_raw + (it % STAGES) * STB;
+    unsigned char* sB = sA + NC * U_APL;
+    const int l = l0 + it / ktiles, k0 = (it % ktiles) * UBK;
+    const __half* Al = PA + (size_t)l * NC * planeA;
+    const __half* Bl = PB + (size_t)l * NC * planeB;
+#pragma unroll
+    for (int i = t; i < NC * UBM * 4; i += UTHREADS) {
+      const int c = i / (UBM * 4), rem = i % (UBM * 4), r = rem >> 2, kg = rem & 3;
+      const bool ok = (m0 + r) < M;
+      const __half* src = Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + kg * 8;
+      cp16(sA + c * U_APL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
+    }
+#pragma unroll
+    for (int i = t; i < NC * UBN * 4; i += UTHREADS) {
+      const int c = i / (UBN * 4), rem = i % (UBN * 4), r = rem >> 2, kg = rem & 3;
+      const bool ok = (n0 + r) < N;
+      const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + kg * 8;
+      cp16(sB + c * U_BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
+    }
+  };
+
+  // running residues of this thread's row (32 q + lane) and 64 columns (64 h + x)
+  float res[NC][64];
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[c][a][b][q] = 0.f;
-#pragma unroll
-  for (int c = 0; c < NCOUT; ++c)
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) res[c][a][b][q] = 0.f;
+    for (int x = 0; x < 64; ++x) res[c][x] = 0.f;
 
-  auto load = [&](int stage, int k0) {
-    __half* As = sm + stage * ST;
-    __half* Bs = As + A_ST;
-    // A: NC * 128 rows * 4 chunks of 16 B
-    for (int i = t; i < NC * CBM * 4; i += CNT) {
-      const int c = i / (CBM * 4), rem = i % (CBM * 4), r = rem >> 2, ch = rem & 3;
-      const bool ok = (m0 + r) < M;
-      const __half* src = Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + ch * 8;
-      cp16(As + (c * CBM + r) * KPAD + ch * 8, src, ok);
+  auto epilogue = [&](int u) {
+    const int b = u & 1;
+    if (!mbar_wait(smem_addr(bars + STAGES + b), (unsigned)(u >> 1) & 1u)) {
+      *sabort = 1;
+      if (status) set_err_once(status, GBHE_ETIMEOUT);
     }
-    for (int i = t; i < NC * CBN * 4; i += CNT) {
-      const int c = i / (CBN * 4), rem = i % (CBN * 4), r = rem >> 2, ch = rem & 3;
-      const bool ok = (n0 + r) < N;
-      const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + ch * 8;
-      cp16(Bs + (c * CBN + r) * KPAD + ch * 8, src, ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int l = l0 + u / nch;
+    const float p = (float)c_p[l], pinv = c_pinv[l];
+    const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(64 * h);
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+      float P[NC][16];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int x = 0; x < 16; ++x) res[c][sl * 16 + x] += red_sym(P[c][x], p, pinv);
     }
-  };
-
-  // Fold one exact chunk into the running residues.  The running sums are
-  // kept as unreduced integers (each chunk adds at most 2p + 2 in magnitude,
-  // and K <= 2^16 gives at most 128 chunks), reduced once at the end.
-  auto flush = [&]() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if ((u % nch) == nch - 1) {
+      const int il = 32 * q + lane;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int x = 0; x < 64; ++x) {
+        const int jl = 64 * h + x;
 #pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (CPLX) {
-            const float p1 = acc[0][a][b][q], p2 = acc[1][a][b][q], p3 = acc[2][a][b][q];
-            // |p_i| <= 2^23, so p1 - p2 and p1 + p2 are exact
-            res[0][a][b][q] += red_sym(p1 - p2, p, pinv);
-            res[NCOUT - 1][a][b][q] += red_sym(p3, p, pinv) - red_sym(p1 + p2, p, pinv);
-          } else {
-            res[0][a][b][q] += red_sym(acc[0][a][b][q], p, pinv);
-          }
-#pragma unroll
-          for (int c = 0; c < NC; ++c) acc[c][a][b][q] = 0.f;
-        }
-  };
-
-  const int ktiles = Kp / CBK;
-#pragma unroll
-  for (int s = 0; s < CSTAGE - 1; ++s) {
-    if (s < ktiles) load(s, s * CBK);
-    cp_commit();
-  }
-  for (int kt = 0; kt < ktiles; ++kt) {
-    cp_wait<CSTAGE - 2>();
-    __syncthreads();
-    {
-      const int ks = kt + CSTAGE - 1;
-      if (ks < ktiles) load(ks % CSTAGE, ks * CBK);
-      cp_commit();
-    }
-    const __half* As = sm + (kt % CSTAGE) * ST;
-    const __half* Bs = As + A_ST;
-#pragma unroll
-    for (int kk = 0; kk < CBK; kk += 16) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        unsigned af[2][4], bf[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          // ldmatrix.x4 of the 16x16 A tile: lanes 0-15 rows 0-15 (k 0-7), lanes 16-31 rows 0-15 (k 8-15)
-          const int row = wm + mt * 16 + (lane & 15);
-          const int col = kk + ((lane >> 4) << 3);
-          ldsm_x4(af[mt], As + (c * CBM + row) * KPAD + col);
-        }
-#pragma unroll
-        for (int np = 0; np < 2; ++np) {
-          // two n8 tiles: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
-          const int nrow = wn + np * 16 + (lane & 7) + ((lane >> 4) << 3);
-          const int col = kk + (((lane >> 3) & 1) << 3);
-          ldsm_x4(bf[np], Bs + (c * CBN + nrow) * KPAD + col);
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
-            hmma(acc[c][mt][nt], af[mt], bf[nt >> 1][(nt & 1) * 2], bf[nt >> 1][(nt & 1) * 2 + 1]);
-      }
-    }
-    if (((kt + 1) * CBK) % KC == 0) flush();
-  }
-  cp_wait<0>();
-  if ((ktiles * CBK) % KC != 0) flush();
-  __syncthreads();  // every warp is done with the operand stages: reuse them for the output tile
-  // Reduce to [0, p) and stage the bytes column-major in shared memory.  Element
-  // q of the 16x8 fragment: row g + 8 (q >> 1), column 2 tq + (q & 1).
-  unsigned char* stile = smem_raw;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int il = wm + a * 16 + (lane >> 2) + 8 * (q >> 1);
-        const int jl = wn + b * 8 + 2 * (lane & 3) + (q & 1);
-#pragma unroll
-        for (int c = 0; c < NCOUT; ++c) {
-          float v = red_sym(res[c][a][b][q], p, pinv);
+        for (int c = 0; c < NC; ++c) {
+          float v = red_sym(res[c][x], p, pinv);
           if (v < 0.f) v += p;
           if (v >= p) v -= p;
-          stile[(c * CBN + jl) * OPITCH + il] = (unsigned char)(int)v;
+          stile[(c * UBN + jl) * OPITCH + il] = (unsigned char)(int)v;
+          res[c][x] = 0.f;
         }
       }
-  __syncthreads();
-  unsigned char* dst = Out + ((size_t)(blockIdx.y * TM + blockIdx.x) * NMOD + l) * NCOUT * OTILE;
-  // only the 16-row chunks and columns that hold outputs (the rest is never read)
-  const int nu = (min(CBM, M - m0) + 15) / 16, ncol = min(CBN, N - n0);
-  for (int i = t; i < NCOUT * ncol * nu; i += CNT) {
-    const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, u = rem % nu;
-    const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * CBN + jl) * OPITCH + u * 16);
-    *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + jl) * CBM + u * 16) = v;
+      __syncthreads();
+      // the two CBN-wide layout tiles of this CTA
+      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
+      for (int i = t; i < NC * ncol * nu; i += UTHREADS) {
+        const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, uu = rem % nu;
+        const int tile = (2 * by + jl / CBN) * TM + bx;
+        unsigned char* dst = Out + ((size_t)tile * NMOD + l) * NC * OTILE;
+        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * UBN + jl) * OPITCH + uu * 16);
+        *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + (jl % CBN)) * CBM + uu * 16) = v;
+      }
+    }
+  };
+
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < iters) load(s);
+    cp_commit();
   }
+  bool aborted = false;
+  for (int it = 0; it < iters; ++it) {
+    const int s = it % STAGES;
+    const int kt = it % ktiles;
+    const int u = (it / ktiles) * nch + kt / KTC;
+    const bool unit_start = (kt % KTC) == 0;
+    cp_wait<STAGES - 2>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (*sabort) { aborted = true; break; }
+    if (t == 0) {
+      const unsigned dbuf = tmem + (unsigned)(u & 1) * CF::BUFC;
+      const unsigned sA = smem_addr(smem_raw + s * STB), sB = sA + NC * U_APL;
+#pragma unroll
+      for (int kk = 0; kk < UBK / 16; ++kk) {
+        const unsigned first = (unit_start && kk == 0) ? 0u : 1u;
+        const unsigned long long ar = umma_sdesc(sA + kk * 256, 128, 512);
+        const unsigned long long br = umma_sdesc(sB + kk * 256, 128, 512);
+        umma_f16(dbuf, ar, br, idesc, first);  // Re (or the real product) += Ar Br
+        if constexpr (CPLX) {
+          const unsigned long long ai = umma_sdesc(sA + U_APL + kk * 256, 128, 512);
+          const unsigned long long bi = umma_sdesc(sB + U_BPL + kk * 256, 128, 512);
+          umma_f16(dbuf, ai, bi, idesc_negA, 1u);     // Re -= Ai Bi
+          umma_f16(dbuf + UBN, ar, bi, idesc, first);  // Im += Ar Bi
+          umma_f16(dbuf + UBN, ai, br, idesc, 1u);     // Im += Ai Br
+        }
+      }
+      umma_commit(smem_addr(bars + s));
+      if ((kt % KTC) == KTC - 1 || kt == ktiles - 1) umma_commit(smem_addr(bars + STAGES + (u & 1)));
+    }
+    // refill the stage read by the previous iteration's products
+    if (it + STAGES - 1 < iters) {
+      if (it >= 1 && !mbar_wait(smem_addr(bars + (it - 1) % STAGES), (unsigned)((it - 1) / STAGES) & 1u)) {
+        *sabort = 1;
+        if (status) set_err_once(status, GBHE_ETIMEOUT);
+      }
+      load(it + STAGES - 1);
+    }
+    cp_commit();
+    if (unit_start && u > 0) epilogue(u - 1);
+  }
+  if (!aborted) epilogue(mpc * nch - 1);
+  cp_wait<0>();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CF::COLS));
 }
 
 // ------------------------------------------------------------------ reconstruction
@@ -705,9 +799,35 @@ inline size_t out_bytes(int M, int N, int cplx) {
   return (size_t)((M + CBM - 1) / CBM) * ((N + CBN - 1) / CBN) * NMOD * (cplx ? 2 : 1) * OTILE;
 }
 
+// Launch of the tcgen05 residue products: moduli per CTA chosen so that the
+// grid covers the GPU at least twice.
+template <bool CPLX>
+int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
+                const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
+  const size_t smem = UCfg<CPLX>::SMEM;
+  static bool attr = false;
+  static int nsm = 0;
+  if (!attr) {
+    GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0;
+    GBHE_CUDA(cudaGetDevice(&dev));
+    GBHE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr = true;
+  }
+  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
+  const long tiles = (long)TM * TN2 * nbatch;
+  // moduli per CTA: as many as keep at least two CTAs per SM
+  int mpc = NMOD;
+  while (mpc > 1 && tiles * (NMOD / mpc) < 2L * nsm) mpc /= 2;
+  dim3 grid(TM * TN2, 1, (NMOD / mpc) * nbatch);
+  k_crt_umma<CPLX><<<grid, UTHREADS, smem, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc, status);
+  count_launch();
+  return 0;
+}
+
 size_t crt_bytes(int M, int N, int K, int cplx) {
   const size_t Kp = (size_t)(K + CBK - 1) / CBK * CBK;
-  const int nc = cplx ? 3 : 1;
+  const int nc = cplx ? 2 : 1;
   size_t b = 0;
   b += (size_t)NMOD * nc * (size_t)M * Kp * 2 + 256;
   b += (size_t)NMOD * nc * (size_t)N * Kp * 2 + 256;
@@ -730,7 +850,7 @@ size_t crt_gemm_ws_bytes(int M, int N, int K, int cplx) { return crt_bytes(M, N,
 
 size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) {
   const size_t Kp = (size_t)(maxK + CBK - 1) / CBK * CBK;
-  const int nc = cplx ? 3 : 1;
+  const int nc = cplx ? 2 : 1;
   const size_t nbt = (size_t)std::max(nbatch, 1);
   size_t b = 0;
   b += nbt * NMOD * nc * (size_t)maxM * Kp * 2 + 256;
@@ -741,14 +861,14 @@ size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) 
 }
 
 int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, int cplx_flag, const CrtDesc* D,
-                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes) {
+                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes, int* status) {
   if (nbatch <= 0 || maxM <= 0 || maxN <= 0 || maxK <= 0) return 0;
   if (maxK > KMAX || nbatch > 65535 / NMOD) return GBHE_EWORKSPACE;
   if (crt_batched_ws_bytes(nbatch, maxM, maxN, maxK, cplx_flag) > ws_bytes) return GBHE_EWORKSPACE;
   int rc = init_constants();
   if (rc) return rc;
   const int Kp = (maxK + CBK - 1) / CBK * CBK;
-  const int nc = cplx_flag ? 3 : 1;
+  const int nc = cplx_flag ? 2 : 1;
   char* p = reinterpret_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
   __half* PA = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxM * Kp * 2));
@@ -769,23 +889,9 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   count_launch();
   k_bop_residues<<<dim3((maxN + 31) / 32, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, 0, opB, cplx_flag, maxN, eb, Kp, PB);
   count_launch();
-  const size_t smem = (size_t)CSTAGE * nc * (CBM + CBN) * KPAD * sizeof(__half);
-  static bool attr_c = false, attr_r = false;
-  dim3 grid((maxM + CBM - 1) / CBM, (maxN + CBN - 1) / CBN, NMOD * nbatch);
-  if (cplx_flag) {
-    if (!attr_c) {
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_c = true;
-    }
-    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0);
-  } else {
-    if (!attr_r) {
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_r = true;
-    }
-    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0);
-  }
-  count_launch();
+  rc = cplx_flag ? launch_umma<true>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status)
+                 : launch_umma<false>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status);
+  if (rc) return rc;
   const size_t total = (size_t)nbatch * out_bytes(maxM, maxN, 0) / NMOD / 4;  // four outputs per thread
   k_bcrt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, D, nbatch, maxM, maxN,
                                                                                            ea, eb, alpha, beta,
@@ -848,7 +954,7 @@ int gemm(Ctx& c, const GemmArgs& g, int cplx) {
         if (g.opB == OP_N) s.B = B + ((size_t)k0 + (size_t)j0 * g.ldb) * es;
         else s.B = B + ((size_t)j0 + (size_t)k0 * g.ldb) * es;
         s.C = reinterpret_cast<char*>(g.C) + ((size_t)i0 + (size_t)j0 * g.ldc) * es;
-        int rc = crt_gemm(c.st, s, cplx, c.crt_ws, c.crt_ws_bytes);
+        int rc = crt_gemm(c.st, s, cplx, c.crt_ws, c.crt_ws_bytes, c.status);
         if (rc) return rc;
       }
     }
@@ -856,14 +962,14 @@ int gemm(Ctx& c, const GemmArgs& g, int cplx) {
   return 0;
 }
 
-int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes) {
+int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes, int* status) {
   if (g.m <= 0 || g.n <= 0) return 0;
   if (g.k <= 0 || g.k > KMAX) return GBHE_EWORKSPACE;
   int rc = init_constants();
   if (rc) return rc;
   const int M = g.m, N = g.n, K = g.k;
   const int Kp = (K + CBK - 1) / CBK * CBK;
-  const int nc = cplx ? 3 : 1;
+  const int nc = cplx ? 2 : 1;
   if (crt_bytes(M, N, K, cplx) > ws_bytes) return GBHE_EWORKSPACE;
   char* p = reinterpret_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
@@ -888,23 +994,9 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
   count_launch();
   k_op_residues<<<dim3((N + 31) / 32, Kp / 32), dim3(32, 8), 0, st>>>(ob, eb, Kp, PB);
   count_launch();
-  const size_t smem = (size_t)CSTAGE * nc * (CBM + CBN) * KPAD * sizeof(__half);
-  static bool attr_c = false, attr_r = false;
-  dim3 grid((M + CBM - 1) / CBM, (N + CBN - 1) / CBN, NMOD);
-  if (cplx) {
-    if (!attr_c) {
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_c = true;
-    }
-    k_crt_mma<true><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only);
-  } else {
-    if (!attr_r) {
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_r = true;
-    }
-    k_crt_mma<false><<<grid, CNT, smem, st>>>(PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only);
-  }
-  count_launch();
+  rc = cplx ? launch_umma<true>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status)
+            : launch_umma<false>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status);
+  if (rc) return rc;
   const size_t total = out_bytes(M, N, 0) / NMOD / 4;  // four outputs per thread
   k_crt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, M, N, ea, eb, g, cplx);
   count_launch();

@@ -49,9 +49,10 @@ class ProfScope {
   void* ev_;
 };
 
-// FP64-exact GEMM on the FP16 tensor cores (crt.cu); workspace passed explicitly.
+// FP64-exact GEMM on the FP16 tensor cores (crt.cu); workspace passed
+// explicitly; an expired bounded wait records GBHE_ETIMEOUT in status[ST_ERR].
 size_t crt_gemm_ws_bytes(int M, int N, int K, int cplx);
-int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes);
+int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_bytes, int* status);
 
 // Batched form: entry z computes C_z = alpha op(A_z) op(B_z) + beta C_z with
 // its own sizes (M_z <= maxM, N_z <= maxN, K_z <= maxK) and pointers; the
@@ -65,7 +66,7 @@ struct CrtDesc {
 };
 size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx);
 int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, int cplx_flag, const CrtDesc* d_desc,
-                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes);
+                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes, int* status);
 
 size_t dense_ws_bytes(int n);
 int potrf_run(Ctx& c, int n, cplx* B, int ldb);
