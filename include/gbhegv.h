@@ -79,6 +79,14 @@ int gbhe_default_nb(int n);
 #define GBHE_ENGINE_CRT 1
 int gbhe_set_gemm_engine(gbhe_handle h, int engine);
 
+/* Largest block (in every dimension) of one tensor-core GEMM call, 128 ..
+ * 16384 (the default).  Larger products are cut into blocks of this size.
+ * The workspace reported by gbhe_workspace_size grows with the square of
+ * min(n, block) (about 16 GB at n = 10000 with the default); a smaller block
+ * trades speed for memory.  Set it before gbhe_workspace_size.  No
+ * counterpart in the paper.  Returns 0, -1 (no handle) or -2 (out of range). */
+int gbhe_set_crt_block(gbhe_handle h, int block);
+
 /* Algorithm 1, step 1 (paper Section 3): Cholesky factorisation B = L L^H.
  * B (n x n, ldb) lower triangle read; L overwrites it (upper untouched).
  * A non-positive pivot at order k sets status k (first failure wins). */

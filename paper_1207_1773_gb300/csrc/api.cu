@@ -22,7 +22,9 @@ int default_nb(int n) {
 
 // Workspace every call carves first: split-K scratch and the diagonal-block
 // inverses.
-size_t common_bytes(int n) { return GEMM_SCRATCH_BYTES + dense_ws_bytes(n) + crt_budget_bytes(n) + 1024; }
+size_t common_bytes(gbhe_handle h, int n) {
+  return GEMM_SCRATCH_BYTES + dense_ws_bytes(n) + crt_budget_bytes(n, h->crt_block) + 1024;
+}
 
 size_t stage_bytes(gbhe_handle h, int n, int nb, int m) {
   size_t s = 0;
@@ -64,10 +66,11 @@ int make_ctx(gbhe_handle h, int n, void* stream, Ctx* c) {
   c->dense_scratch = c->arena.take<cplx>(dense_ws_bytes(n) / sizeof(cplx));
   if (!c->arena.ok() || !c->gemm_scratch) return GBHE_EWORKSPACE;
   c->engine = h->engine;
+  c->crt_block = h->crt_block;
   c->crt_ws = nullptr;
   c->crt_ws_bytes = 0;
   if (h->engine == GBHE_ENGINE_CRT) {
-    const size_t cb = crt_budget_bytes(n);
+    const size_t cb = crt_budget_bytes(n, h->crt_block);
     const size_t save = c->arena.off;
     char* ws = c->arena.take<char>(cb);
     if (c->arena.ok() && ws) {
@@ -97,6 +100,13 @@ int gbhe_set_gemm_engine(gbhe_handle h, int engine) {
   return 0;
 }
 
+int gbhe_set_crt_block(gbhe_handle h, int block) {
+  if (!h) return -1;
+  if (block < 128 || block > CRT_BLOCK) return -2;
+  h->crt_block = block;
+  return 0;
+}
+
 unsigned long long gbhe_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 int gbhe_create(gbhe_handle* handle, int device) {
@@ -118,6 +128,7 @@ int gbhe_create(gbhe_handle* handle, int device) {
   h->work_bytes = 0;
   h->spin_limit = 0;
   h->engine = GBHE_ENGINE_CRT;
+  h->crt_block = CRT_BLOCK;
   *handle = h;
   return 0;
 }
@@ -138,7 +149,7 @@ int gbhe_workspace_size(gbhe_handle h, int n, int nb, int m, size_t* bytes) {
   if (nb < 1 || nb > 128) return -3;
   if (m < 0 || m > n) return -4;
   if (!bytes) return -5;
-  *bytes = common_bytes(n) + driver_bytes(n, nb, m) + stage_bytes(h, n, nb, m) + 4096;
+  *bytes = common_bytes(h, n) + driver_bytes(n, nb, m) + stage_bytes(h, n, nb, m) + 4096;
   return 0;
 }
 

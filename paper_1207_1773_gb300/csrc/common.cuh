@@ -141,6 +141,7 @@ struct gbhe_ctx {
   size_t work_bytes;
   unsigned spin_limit;  // test hook (0 = default)
   int engine;           // GBHE_ENGINE_CRT (default) or GBHE_ENGINE_DMMA
+  int crt_block;        // largest tensor-core GEMM block (workspace vs speed)
 };
 
 #define GBHE_CUDA(call)                                      \

@@ -149,7 +149,11 @@ __device__ __forceinline__ void op_exponents_tile(const Operand& o, int* e, int 
   }
 }
 
-__global__ void k_op_exponents(Operand o, int* e) { op_exponents_tile(o, e, blockIdx.x, blockIdx.y); }
+// Both operands in one launch: blocks x < gA take op(A), the rest op(B).
+__global__ void k_op_exponents(Operand oa, int* ea, Operand ob, int* eb, int gA) {
+  const bool isA = blockIdx.x < (unsigned)gA;
+  op_exponents_tile(isA ? oa : ob, isA ? ea : eb, isA ? blockIdx.x : blockIdx.x - gA, blockIdx.y);
+}
 
 __global__ void k_fill_int(int* p, int n, int v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
@@ -228,8 +232,10 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
   }
 }
 
-__global__ void k_op_residues(Operand o, const int* e, int Kp, __half* P) {
-  op_residues_tile(o, e, Kp, P, blockIdx.x, blockIdx.y);
+__global__ void k_op_residues(Operand oa, const int* ea, __half* PA, Operand ob, const int* eb, __half* PB, int gA,
+                              int Kp) {
+  const bool isA = blockIdx.x < (unsigned)gA;
+  op_residues_tile(isA ? oa : ob, isA ? ea : eb, Kp, isA ? PA : PB, isA ? blockIdx.x : blockIdx.x - gA, blockIdx.y);
 }
 
 // ---- batched forms: entry z of a device descriptor array per blockIdx.z
@@ -247,16 +253,24 @@ __device__ __forceinline__ Operand desc_operand(const CrtDesc& d, int isA, int o
   return o;
 }
 
-__global__ void k_bop_exponents(const CrtDesc* D, int isA, int op, int cplx, int maxR, int* e) {
-  const Operand o = desc_operand(D[blockIdx.z], isA, op, cplx);
-  op_exponents_tile(o, e + (size_t)blockIdx.z * maxR, blockIdx.x, blockIdx.y);
+// Both operands of every entry in one launch: blocks x < gA = ceil(maxM/32)
+// take op(A_z), the rest op(B_z).
+__global__ void k_bop_exponents(const CrtDesc* D, int opA, int opB, int cplx, int maxM, int maxN, int* ea, int* eb,
+                                int gA) {
+  const bool isA = blockIdx.x < (unsigned)gA;
+  const Operand o = desc_operand(D[blockIdx.z], isA ? 1 : 0, isA ? opA : opB, cplx);
+  int* e = isA ? ea + (size_t)blockIdx.z * maxM : eb + (size_t)blockIdx.z * maxN;
+  op_exponents_tile(o, e, isA ? blockIdx.x : blockIdx.x - gA, blockIdx.y);
 }
 
-__global__ void k_bop_residues(const CrtDesc* D, int isA, int op, int cplx, int maxR, const int* e, int Kp,
-                               __half* P) {
-  const Operand o = desc_operand(D[blockIdx.z], isA, op, cplx);
+__global__ void k_bop_residues(const CrtDesc* D, int opA, int opB, int cplx, int maxM, int maxN, const int* ea,
+                               const int* eb, int Kp, __half* PA, __half* PB, int gA) {
+  const bool isA = blockIdx.x < (unsigned)gA;
+  const Operand o = desc_operand(D[blockIdx.z], isA ? 1 : 0, isA ? opA : opB, cplx);
+  const int maxR = isA ? maxM : maxN;
   const size_t entry = (size_t)NMOD * (cplx ? 2 : 1) * maxR * Kp;
-  op_residues_tile(o, e + (size_t)blockIdx.z * maxR, Kp, P + blockIdx.z * entry, blockIdx.x, blockIdx.y);
+  op_residues_tile(o, (isA ? ea : eb) + (size_t)blockIdx.z * maxR, Kp, (isA ? PA : PB) + blockIdx.z * entry,
+                   isA ? blockIdx.x : blockIdx.x - gA, blockIdx.y);
 }
 
 __global__ void k_fill_int_batched(int* p, size_t n, int v) {
@@ -832,7 +846,7 @@ size_t crt_bytes(int M, int N, int K, int cplx) {
   b += (size_t)NMOD * nc * (size_t)M * Kp * 2 + 256;
   b += (size_t)NMOD * nc * (size_t)N * Kp * 2 + 256;
   b += out_bytes(M, N, cplx) + 256;
-  b += ((size_t)M + N) * sizeof(int) + 512;
+  b += ((size_t)M + N) * sizeof(int) + 256;
   return b;
 }
 
@@ -856,7 +870,7 @@ size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) 
   b += nbt * NMOD * nc * (size_t)maxM * Kp * 2 + 256;
   b += nbt * NMOD * nc * (size_t)maxN * Kp * 2 + 256;
   b += nbt * out_bytes(maxM, maxN, cplx) + 256;
-  b += nbt * ((size_t)maxM + maxN) * sizeof(int) + 512;
+  b += nbt * ((size_t)maxM + maxN) * sizeof(int) + 256;
   return b;
 }
 
@@ -874,20 +888,17 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   __half* PA = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxM * Kp * 2));
   __half* PB = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxN * Kp * 2));
   unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)nbatch * out_bytes(maxM, maxN, cplx_flag)));
-  int* ea = reinterpret_cast<int*>(take((size_t)nbatch * maxM * sizeof(int)));
-  int* eb = reinterpret_cast<int*>(take((size_t)nbatch * maxN * sizeof(int)));
+  int* ea = reinterpret_cast<int*>(take((size_t)nbatch * (maxM + maxN) * sizeof(int)));
+  int* eb = ea + (size_t)nbatch * maxM;
   ProfScope prof(st, GBHE_PROF_CRT, 0.0, 0.0);
-  k_fill_int_batched<<<256, 256, 0, st>>>(ea, (size_t)nbatch * maxM, -1100);
+  k_fill_int_batched<<<256, 256, 0, st>>>(ea, (size_t)nbatch * (maxM + maxN), -1100);
   count_launch();
-  k_fill_int_batched<<<256, 256, 0, st>>>(eb, (size_t)nbatch * maxN, -1100);
+  const int gA = (maxM + 31) / 32, gB = (maxN + 31) / 32;
+  k_bop_exponents<<<dim3(gA + gB, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, opA, opB, cplx_flag, maxM, maxN,
+                                                                                   ea, eb, gA);
   count_launch();
-  k_bop_exponents<<<dim3((maxM + 31) / 32, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, 1, opA, cplx_flag, maxM, ea);
-  count_launch();
-  k_bop_exponents<<<dim3((maxN + 31) / 32, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, 0, opB, cplx_flag, maxN, eb);
-  count_launch();
-  k_bop_residues<<<dim3((maxM + 31) / 32, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, 1, opA, cplx_flag, maxM, ea, Kp, PA);
-  count_launch();
-  k_bop_residues<<<dim3((maxN + 31) / 32, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, 0, opB, cplx_flag, maxN, eb, Kp, PB);
+  k_bop_residues<<<dim3(gA + gB, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, opA, opB, cplx_flag, maxM, maxN, ea, eb,
+                                                                         Kp, PA, PB, gA);
   count_launch();
   rc = cplx_flag ? launch_umma<true>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status)
                  : launch_umma<false>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status);
@@ -900,8 +911,8 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
 }
 
-size_t crt_budget_bytes(int n) {
-  const int b = std::max(1, std::min(n, CRT_BLOCK));
+size_t crt_budget_bytes(int n, int block) {
+  const int b = std::max(1, std::min(n, block));
   // at least 64 MiB: the batched products of small problems (one padded
   // 128 x 64 output tile per entry) need more than an n x n x n product
   return std::max(crt_bytes(b, b, b, 1), size_t(64) << 20);
@@ -914,7 +925,7 @@ int gemm(Ctx& c, const GemmArgs& g, int cplx) {
   if (!use_crt) return cplx ? zgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes)
                             : dgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes);
   // blocks of at most CRT_BLOCK in every dimension; K blocks accumulate in C
-  const int bm = std::min(g.m, CRT_BLOCK), bn = std::min(g.n, CRT_BLOCK), bk = std::min(g.k, CRT_BLOCK);
+  const int bm = std::min(g.m, c.crt_block), bn = std::min(g.n, c.crt_block), bk = std::min(g.k, c.crt_block);
   // element size in bytes (the int parameter `cplx` shadows the type name here)
   const size_t es = cplx ? sizeof(double2) : sizeof(double);
   const bool herm = (g.opA == OP_H);
@@ -976,23 +987,18 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
   __half* PA = reinterpret_cast<__half*>(take((size_t)NMOD * nc * M * Kp * 2));
   __half* PB = reinterpret_cast<__half*>(take((size_t)NMOD * nc * N * Kp * 2));
   unsigned char* Out = reinterpret_cast<unsigned char*>(take(out_bytes(M, N, cplx)));
-  int* ea = reinterpret_cast<int*>(take((size_t)M * sizeof(int)));
-  int* eb = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
+  int* ea = reinterpret_cast<int*>(take((size_t)(M + N) * sizeof(int)));
+  int* eb = ea + M;
   const Operand oa = make_operand(g.A, g.lda, M, K, g.opA, true, cplx);
   const Operand ob = make_operand(g.B, g.ldb, N, K, g.opB, false, cplx);
   const double flops = (cplx ? 8.0 : 2.0) * (double)M * N * K;
   ProfScope prof(st, GBHE_PROF_CRT, flops, 0.0);
-  k_fill_int<<<64, 256, 0, st>>>(ea, M, -1100);
+  k_fill_int<<<64, 256, 0, st>>>(ea, M + N, -1100);
   count_launch();
-  k_fill_int<<<64, 256, 0, st>>>(eb, N, -1100);
+  const int gA = (M + 31) / 32, gB = (N + 31) / 32;
+  k_op_exponents<<<dim3(gA + gB, (K + 31) / 32), dim3(32, 8), 0, st>>>(oa, ea, ob, eb, gA);
   count_launch();
-  k_op_exponents<<<dim3((M + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(oa, ea);
-  count_launch();
-  k_op_exponents<<<dim3((N + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(ob, eb);
-  count_launch();
-  k_op_residues<<<dim3((M + 31) / 32, Kp / 32), dim3(32, 8), 0, st>>>(oa, ea, Kp, PA);
-  count_launch();
-  k_op_residues<<<dim3((N + 31) / 32, Kp / 32), dim3(32, 8), 0, st>>>(ob, eb, Kp, PB);
+  k_op_residues<<<dim3(gA + gB, Kp / 32), dim3(32, 8), 0, st>>>(oa, ea, PA, ob, eb, PB, gA, Kp);
   count_launch();
   rc = cplx ? launch_umma<true>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status)
             : launch_umma<false>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status);

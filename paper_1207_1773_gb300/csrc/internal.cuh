@@ -17,14 +17,16 @@ struct Ctx {
   void* crt_ws;               // residue planes of the tensor-core FP64 GEMM
   size_t crt_ws_bytes;
   int engine;                 // GBHE_ENGINE_DMMA or GBHE_ENGINE_CRT
+  int crt_block;              // largest block of the tensor-core GEMM
   Arena arena;                // the rest, for stage temporaries
 };
 
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(32) << 20;
-// Workspace of the tensor-core FP64 GEMM: enough for 4096 x 4096 x 4096
-// complex blocks; larger products are cut into blocks of that size.
-constexpr int CRT_BLOCK = 4096;
-size_t crt_budget_bytes(int n);
+// Workspace of the tensor-core FP64 GEMM: enough for one complex product of
+// min(n, block) in every dimension (about 16 GB at n = 10000 with the default
+// block); larger products are cut into blocks of that size.
+constexpr int CRT_BLOCK = 16384;
+size_t crt_budget_bytes(int n, int block);
 
 // FP64 GEMM through the engine selected on the handle: exact modular products
 // on the FP16 tensor cores for large products, DMMA otherwise.

@@ -69,6 +69,7 @@ def _load():
             "gbhe_zgemm": ([P, I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
             "gbhe_crt_workspace_size": ([I, I, I, I, ctypes.POINTER(S)], I),
             "gbhe_set_gemm_engine": ([P, I], I),
+            "gbhe_set_crt_block": ([P, I], I),
             "gbhe_gemm_crt": ([P, I, I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
             "gbhe_launch_count": ([], ctypes.c_ulonglong),
             "gbhe_profile_enable": ([I], I),
@@ -96,7 +97,7 @@ def exported_symbols():
                         "gbhe_trsm_lh", "gbhe_hegv", "gbhe_hegv_onestage", "gbhe_status_string",
                         "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
-                        "gbhe_set_gemm_engine", "gbhe_zgemm_static")]
+                        "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block")]
 
 
 def status_string(code: int) -> str:
@@ -329,6 +330,13 @@ def set_engine(name, device=None):
     h = handle(device)
     _check("gbhe_set_gemm_engine", _load().gbhe_set_gemm_engine(h.h, ENGINES[name]))
     h.engine = name
+
+
+def set_crt_block(block=16384, device=None):
+    """Largest block of one tensor-core GEMM call (128..16384); smaller blocks
+    need less workspace and run slower."""
+    h = handle(device)
+    _check("gbhe_set_crt_block", _load().gbhe_set_crt_block(h.h, int(block)))
 
 
 def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):

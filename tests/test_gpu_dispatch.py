@@ -1,5 +1,5 @@
-"""The engine dispatcher cuts products larger than one CRT block (4096 in any
-dimension) into blocks; these shapes exercise every block kind (interior,
+"""The engine dispatcher cuts products larger than one CRT block into blocks;
+with the block set to 4096 these shapes exercise every block kind (interior,
 ragged edge, Hermitian diagonal/off-diagonal, lower-only diagonal, K blocks
 accumulated in C) against numpy FP64."""
 import numpy as np
@@ -17,7 +17,9 @@ def G():
         pytest.skip("no CUDA device")
     from paper_1207_1773_gb300 import gbhegv
     gbhegv.set_engine("crt")
-    return gbhegv
+    gbhegv.set_crt_block(4096)
+    yield gbhegv
+    gbhegv.set_crt_block(16384)
 
 
 @pytest.mark.parametrize("opA,opB,m,n,k,lower", [
