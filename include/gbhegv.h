@@ -223,7 +223,10 @@ unsigned long long gbhe_launch_count(void);
 #define GBHE_PROF_STEDC 5  /* tridiagonal divide and conquer (whole call)  */
 #define GBHE_PROF_HEMV 6   /* one-stage Hermitian matrix-vector products   */
 #define GBHE_PROF_CRT 7    /* FP64-exact GEMM on FP16 tensor cores (CRT)   */
-#define GBHE_PROF_NCLASS 8
+#define GBHE_PROF_CRT_PREP 8  /* CRT: exponents and residues of the operands */
+#define GBHE_PROF_CRT_MMA 9   /* CRT: residue products (tcgen05)             */
+#define GBHE_PROF_CRT_REC 10  /* CRT: reconstruction and update of C         */
+#define GBHE_PROF_NCLASS 11
 int gbhe_profile_enable(int on);
 int gbhe_profile_read(int cls, unsigned long long* launches, double* flops, double* bytes, double* ms);
 

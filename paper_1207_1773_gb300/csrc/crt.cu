@@ -48,7 +48,8 @@ __constant__ float c_pinv[NMOD];
 __constant__ float c_frac[NMOD];         // y_l / p_l
 __constant__ unsigned c_W[NMOD][4];      // W_l (128-bit, little-endian words)
 __constant__ unsigned c_M[4];            // M
-__constant__ int c_k18[NMOD], c_k36[NMOD];  // 2^18 mod p, 2^36 mod p
+__constant__ unsigned c_k18[NMOD], c_k36[NMOD];  // 2^18 mod p, 2^36 mod p
+__constant__ unsigned c_bm[NMOD];                // floor(2^32 / p) (Barrett reduction)
 
 bool g_const_ready = false;
 
@@ -57,7 +58,8 @@ int init_constants() {
   typedef unsigned __int128 u128;
   u128 M = 1;
   for (int l = 0; l < NMOD; ++l) M *= (u128)h_mod[l];
-  int p[NMOD], k18[NMOD], k36[NMOD];
+  int p[NMOD];
+  unsigned k18[NMOD], k36[NMOD], bm[NMOD];
   float pinv[NMOD], frac[NMOD];
   unsigned W[NMOD][4], Mw[4];
   for (int l = 0; l < NMOD; ++l) {
@@ -72,8 +74,9 @@ int init_constants() {
     p[l] = pl;
     pinv[l] = 1.0f / (float)pl;
     frac[l] = (float)((double)y / (double)pl);
-    k18[l] = (int)(((u128)1 << 18) % (u128)pl);
-    k36[l] = (int)(((u128)1 << 36) % (u128)pl);
+    k18[l] = (unsigned)(((u128)1 << 18) % (u128)pl);
+    k36[l] = (unsigned)(((u128)1 << 36) % (u128)pl);
+    bm[l] = (unsigned)(((u128)1 << 32) / (u128)pl);
   }
   for (int w = 0; w < 4; ++w) Mw[w] = (unsigned)(M >> (32 * w));
   GBHE_CUDA(cudaMemcpyToSymbol(c_p, p, sizeof(p)));
@@ -83,6 +86,7 @@ int init_constants() {
   GBHE_CUDA(cudaMemcpyToSymbol(c_M, Mw, sizeof(Mw)));
   GBHE_CUDA(cudaMemcpyToSymbol(c_k18, k18, sizeof(k18)));
   GBHE_CUDA(cudaMemcpyToSymbol(c_k36, k36, sizeof(k36)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_bm, bm, sizeof(bm)));
   g_const_ready = true;
   return 0;
 }
@@ -159,15 +163,6 @@ __global__ void k_fill_int(int* p, int n, int v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
-// residue of a non-negative integer x < 2^18 modulo p (fp32 exact arithmetic)
-__device__ __forceinline__ float fmod_small(float x, float p, float pinv) {
-  float q = floorf(x * pinv);
-  float r = fmaf(-q, p, x);
-  if (r < 0.f) r += p;
-  if (r >= p) r -= p;
-  return r;
-}
-
 // Residue planes: P[(l * ncomp + c) * R * Kp + r * Kp + k] (fp16), symmetric
 // residues of the scaled integer of element (r, k); zero for k >= K.
 __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e, int Kp, __half* P, int bx, int by) {
@@ -192,7 +187,9 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
     const double2 v = tile[q][tx];
     const int er = e[r];
     // scaled integers (|v| <= 2^52) as sign + three 18-bit limbs
-    int sg[2], a[2], b[2], c[2];
+    bool sg[2];
+    unsigned a[2], b[2], c[2];
+#pragma unroll
     for (int part = 0; part < 2; ++part) {
       const double x = part ? v.y : v.x;
       const long long bits = __double_as_longlong(x);
@@ -203,31 +200,28 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
         const int sh = er - (E - 1023);  // right shift (>= 1)
         if (sh <= 60) mag = (mant + (1ull << (sh - 1))) >> sh;
       }
-      sg[part] = (bits < 0) ? 1 : 0;
-      a[part] = (int)(mag >> 36);
-      b[part] = (int)((mag >> 18) & 0x3FFFF);
-      c[part] = (int)(mag & 0x3FFFF);
+      sg[part] = bits < 0;
+      a[part] = (unsigned)(mag >> 36);
+      b[part] = (unsigned)((mag >> 18) & 0x3FFFF);
+      c[part] = (unsigned)(mag & 0x3FFFF);
     }
+#pragma unroll
     for (int l = 0; l < NMOD; ++l) {
-      const float p = (float)c_p[l], pinv = c_pinv[l];
-      float rr[2];
+      const unsigned p = (unsigned)c_p[l], bm = c_bm[l], k18 = c_k18[l], k36 = c_k36[l];
+      __half hv[2];
+#pragma unroll
       for (int part = 0; part < 2; ++part) {
-        const float ra = fmod_small((float)a[part], p, pinv);
-        const float rb = fmod_small((float)b[part], p, pinv);
-        const float rc = fmod_small((float)c[part], p, pinv);
-        float t = fmaf(ra, (float)c_k36[l], fmaf(rb, (float)c_k18[l], rc));  // < 2^17
-        t = fmod_small(t, p, pinv);
-        if (sg[part] && t != 0.f) t = p - t;
-        rr[part] = t;  // in [0, p)
+        // t = mag mod-equivalent below 2^27; Barrett: t - p floor(t bm / 2^32) lies in [0, 2p)
+        const unsigned t = a[part] * k36 + b[part] * k18 + c[part];
+        unsigned rr = t - __umulhi(t, bm) * p;
+        if (rr >= p) rr -= p;
+        int sv = rr > (p >> 1) ? (int)rr - (int)p : (int)rr;  // symmetric, |sv| <= 128
+        if (sg[part]) sv = -sv;
+        hv[part] = __int2half_rn(sv);
       }
-      const float half_p = 0.5f * p;
-      float s0 = rr[0] > half_p ? rr[0] - p : rr[0];
       __half* dst = P + (size_t)(l * ncomp) * plane + (size_t)r * Kp + k;
-      dst[0] = __float2half_rn(s0);
-      if (o.cplx) {
-        float s1 = rr[1] > half_p ? rr[1] - p : rr[1];
-        dst[plane] = __float2half_rn(s1);
-      }
+      dst[0] = hv[0];
+      if (o.cplx) dst[plane] = hv[1];
     }
   }
 }
@@ -383,8 +377,9 @@ __device__ __forceinline__ void tmem_ld16(unsigned addr, float (&v)[16]) {
 // planes and outputs are sized for maxM / maxN, the layout inside an entry's
 // planes uses the entry's own M, N.  lower != 0 skips tiles strictly above the
 // diagonal (their outputs are never read).  Timeouts of the bounded waits
-// record GBHE_ETIMEOUT in status[ST_ERR].
-template <bool CPLX>
+// record GBHE_ETIMEOUT in status[ST_ERR].  ONE: every modulus is a single
+// exact chunk (Kp <= KC_TERMS), so no running residues are kept.
+template <bool CPLX, bool ONE>
 __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, const __half* PB, int M, int N, int Kp,
                                                          unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
                                                          int lower, int mpc, int* status) {
@@ -471,11 +466,12 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   };
 
   // running residues of this thread's row (32 q + lane) and 64 columns (64 h + x)
-  float res[NC][64];
+  constexpr int NRES = ONE ? 1 : 64;
+  float res[NC][NRES];
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int x = 0; x < 64; ++x) res[c][x] = 0.f;
+    for (int x = 0; x < NRES; ++x) res[c][x] = 0.f;
 
   auto epilogue = [&](int u) {
     const int b = u & 1;
@@ -487,32 +483,52 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     const int l = l0 + u / nch;
     const float p = (float)c_p[l], pinv = c_pinv[l];
     const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(64 * h);
+    const int il = 32 * q + lane;
+    if constexpr (ONE) {
+      // the modulus' only chunk: reduce straight to bytes
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl) {
-      float P[NC][16];
+      for (int sl = 0; sl < 4; ++sl) {
+        float P[NC][16];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
+        for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int x = 0; x < 16; ++x) res[c][sl * 16 + x] += red_sym(P[c][x], p, pinv);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    if ((u % nch) == nch - 1) {
-      const int il = 32 * q + lane;
+          for (int x = 0; x < 16; ++x) {
+            float v = red_sym(P[c][x], p, pinv);  // |v| <= p/2 + 1
+            if (v < 0.f) v += p;                  // [0, p)
+            stile[(c * UBN + 64 * h + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
+          }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    } else {
 #pragma unroll
-      for (int x = 0; x < 64; ++x) {
-        const int jl = 64 * h + x;
+      for (int sl = 0; sl < 4; ++sl) {
+        float P[NC][16];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          float v = red_sym(res[c][x], p, pinv);
-          if (v < 0.f) v += p;
-          if (v >= p) v -= p;
-          stile[(c * UBN + jl) * OPITCH + il] = (unsigned char)(int)v;
-          res[c][x] = 0.f;
+        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int x = 0; x < 16; ++x) res[c][sl * 16 + x] += red_sym(P[c][x], p, pinv);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if ((u % nch) == nch - 1) {
+#pragma unroll
+        for (int x = 0; x < NRES; ++x) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            float v = red_sym(res[c][x], p, pinv);
+            if (v < 0.f) v += p;  // [0, p)
+            stile[(c * UBN + 64 * h + x) * OPITCH + il] = (unsigned char)(int)v;
+            res[c][x] = 0.f;
+          }
         }
       }
+    }
+    if (ONE || (u % nch) == nch - 1) {
       __syncthreads();
       // the two CBN-wide layout tiles of this CTA
       const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
@@ -581,21 +597,6 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
 }
 
 // ------------------------------------------------------------------ reconstruction
-// 160-bit accumulate: S += c * W (c < 2^8, W 128-bit)
-__device__ __forceinline__ void mac160(unsigned (&S)[5], unsigned c, const unsigned (&W)[4]) {
-  asm("mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
-      "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
-      "madc.lo.cc.u32 %2, %5, %8, %2;\n\t"
-      "madc.lo.cc.u32 %3, %5, %9, %3;\n\t"
-      "addc.u32 %4, %4, 0;\n\t"
-      "mad.hi.cc.u32 %1, %5, %6, %1;\n\t"
-      "madc.hi.cc.u32 %2, %5, %7, %2;\n\t"
-      "madc.hi.cc.u32 %3, %5, %8, %3;\n\t"
-      "madc.hi.u32 %4, %5, %9, %4;"
-      : "+r"(S[0]), "+r"(S[1]), "+r"(S[2]), "+r"(S[3]), "+r"(S[4])
-      : "r"(c), "r"(W[0]), "r"(W[1]), "r"(W[2]), "r"(W[3]));
-}
-
 // value of the 160-bit two's complement integer D times 2^sc, rounded to double
 __device__ __forceinline__ double int160_to_double(unsigned (&D)[5], int sc) {
   const bool negv = (int)D[4] < 0;
@@ -663,37 +664,43 @@ __device__ __forceinline__ const volatile CrtTables* load_tables() {
   return &tb;
 }
 
+// 160-bit value of sum_w X_w 2^(32 w) for four 64-bit column sums X_w < 2^63
+__device__ __forceinline__ void combine160(unsigned (&D)[5], unsigned long long X0, unsigned long long X1,
+                                           unsigned long long X2, unsigned long long X3) {
+  D[0] = (unsigned)X0;
+  unsigned long long t = (X0 >> 32) + X1;
+  D[1] = (unsigned)t;
+  t = (t >> 32) + X2;
+  D[2] = (unsigned)t;
+  t = (t >> 32) + X3;
+  D[3] = (unsigned)t;
+  D[4] = (unsigned)(t >> 32);
+}
+
 __device__ __forceinline__ double crt_value(const volatile CrtTables* tb, const unsigned (&w)[NMOD], int sh, int sc) {
-  unsigned S[5] = {0, 0, 0, 0, 0};
-  float F = 0.f;
+  // S = sum_l c_l W_l as four independent 64-bit word sums (each term < 2^40,
+  // sixteen terms < 2^44), carries propagated once at the end
+  unsigned long long X0 = 0, X1 = 0, X2 = 0, X3 = 0;
+  float F0 = 0.f, F1 = 0.f;
 #pragma unroll
   for (int l = 0; l < NMOD; ++l) {
     const unsigned c = (w[l] >> sh) & 0xFFu;
-    const unsigned W[4] = {tb->W[l][0], tb->W[l][1], tb->W[l][2], tb->W[l][3]};
-    mac160(S, c, W);
-    F = fmaf((float)c, tb->frac[l], F);
+    X0 += (unsigned long long)c * tb->W[l][0];
+    X1 += (unsigned long long)c * tb->W[l][1];
+    X2 += (unsigned long long)c * tb->W[l][2];
+    X3 += (unsigned long long)c * tb->W[l][3];
+    if (l & 1) F1 = fmaf((float)c, tb->frac[l], F1);
+    else F0 = fmaf((float)c, tb->frac[l], F0);
   }
-  const unsigned q = (unsigned)rintf(F);
+  unsigned S[5], qM[5];
+  combine160(S, X0, X1, X2, X3);
+  const unsigned q = (unsigned)rintf(F0 + F1);  // < 2^12
+  combine160(qM, (unsigned long long)q * tb->M[0], (unsigned long long)q * tb->M[1],
+             (unsigned long long)q * tb->M[2], (unsigned long long)q * tb->M[3]);
   // D = S - q M
-  unsigned qM[5] = {0, 0, 0, 0, 0};
-  const unsigned Mw[4] = {tb->M[0], tb->M[1], tb->M[2], tb->M[3]};
-  mac160(qM, q & 0xFFu, Mw);
-  if (q >> 8) {  // q < 2^12
-    unsigned t2[5] = {0, 0, 0, 0, 0};
-    mac160(t2, q >> 8, Mw);
-    // qM += t2 << 8
-    unsigned carry = 0;
-    unsigned sh8[5];
-    sh8[0] = t2[0] << 8;
-    for (int i = 1; i < 5; ++i) sh8[i] = (t2[i] << 8) | (t2[i - 1] >> 24);
-    for (int i = 0; i < 5; ++i) {
-      unsigned long long s = (unsigned long long)qM[i] + sh8[i] + carry;
-      qM[i] = (unsigned)s;
-      carry = (unsigned)(s >> 32);
-    }
-  }
   unsigned D[5];
   unsigned borrow = 0;
+#pragma unroll
   for (int i = 0; i < 5; ++i) {
     const unsigned long long d = (unsigned long long)S[i] - qM[i] - borrow;
     D[i] = (unsigned)d;
@@ -815,26 +822,40 @@ inline size_t out_bytes(int M, int N, int cplx) {
 
 // Launch of the tcgen05 residue products: moduli per CTA chosen so that the
 // grid covers the GPU at least twice.
+template <bool CPLX, bool ONE>
+int umma_prepare(int* nsm_out) {
+  static bool ready = false;
+  static int nsm = 0;
+  if (!ready) {
+    GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)UCfg<CPLX>::SMEM));
+    int dev = 0;
+    GBHE_CUDA(cudaGetDevice(&dev));
+    GBHE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    ready = true;
+  }
+  *nsm_out = nsm;
+  return 0;
+}
+
 template <bool CPLX>
 int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
                 const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
   const size_t smem = UCfg<CPLX>::SMEM;
-  static bool attr = false;
-  static int nsm = 0;
-  if (!attr) {
-    GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0;
-    GBHE_CUDA(cudaGetDevice(&dev));
-    GBHE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    attr = true;
-  }
+  const bool one = Kp <= UCfg<CPLX>::KC_TERMS;
+  int nsm = 0;
+  int rc = one ? umma_prepare<CPLX, true>(&nsm) : umma_prepare<CPLX, false>(&nsm);
+  if (rc) return rc;
   const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
   const long tiles = (long)TM * TN2 * nbatch;
   // moduli per CTA: as many as keep at least two CTAs per SM
   int mpc = NMOD;
   while (mpc > 1 && tiles * (NMOD / mpc) < 2L * nsm) mpc /= 2;
   dim3 grid(TM * TN2, 1, (NMOD / mpc) * nbatch);
-  k_crt_umma<CPLX><<<grid, UTHREADS, smem, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc, status);
+  if (one)
+    k_crt_umma<CPLX, true><<<grid, UTHREADS, smem, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc, status);
+  else
+    k_crt_umma<CPLX, false><<<grid, UTHREADS, smem, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc, status);
   count_launch();
   return 0;
 }
@@ -891,18 +912,25 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   int* ea = reinterpret_cast<int*>(take((size_t)nbatch * (maxM + maxN) * sizeof(int)));
   int* eb = ea + (size_t)nbatch * maxM;
   ProfScope prof(st, GBHE_PROF_CRT, 0.0, 0.0);
-  k_fill_int_batched<<<256, 256, 0, st>>>(ea, (size_t)nbatch * (maxM + maxN), -1100);
-  count_launch();
-  const int gA = (maxM + 31) / 32, gB = (maxN + 31) / 32;
-  k_bop_exponents<<<dim3(gA + gB, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, opA, opB, cplx_flag, maxM, maxN,
-                                                                                   ea, eb, gA);
-  count_launch();
-  k_bop_residues<<<dim3(gA + gB, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, opA, opB, cplx_flag, maxM, maxN, ea, eb,
-                                                                         Kp, PA, PB, gA);
-  count_launch();
-  rc = cplx_flag ? launch_umma<true>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status)
-                 : launch_umma<false>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status);
-  if (rc) return rc;
+  {
+    ProfScope pp(st, GBHE_PROF_CRT_PREP, 0.0, 0.0);
+    k_fill_int_batched<<<256, 256, 0, st>>>(ea, (size_t)nbatch * (maxM + maxN), -1100);
+    count_launch();
+    const int gA = (maxM + 31) / 32, gB = (maxN + 31) / 32;
+    k_bop_exponents<<<dim3(gA + gB, (maxK + 31) / 32, nbatch), dim3(32, 8), 0, st>>>(D, opA, opB, cplx_flag, maxM, maxN,
+                                                                                     ea, eb, gA);
+    count_launch();
+    k_bop_residues<<<dim3(gA + gB, Kp / 32, nbatch), dim3(32, 8), 0, st>>>(D, opA, opB, cplx_flag, maxM, maxN, ea, eb,
+                                                                           Kp, PA, PB, gA);
+    count_launch();
+  }
+  {
+    ProfScope pm(st, GBHE_PROF_CRT_MMA, 0.0, 0.0);
+    rc = cplx_flag ? launch_umma<true>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status)
+                   : launch_umma<false>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status);
+    if (rc) return rc;
+  }
+  ProfScope pr(st, GBHE_PROF_CRT_REC, 0.0, 0.0);
   const size_t total = (size_t)nbatch * out_bytes(maxM, maxN, 0) / NMOD / 4;  // four outputs per thread
   k_bcrt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, D, nbatch, maxM, maxN,
                                                                                            ea, eb, alpha, beta,
@@ -993,16 +1021,23 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
   const Operand ob = make_operand(g.B, g.ldb, N, K, g.opB, false, cplx);
   const double flops = (cplx ? 8.0 : 2.0) * (double)M * N * K;
   ProfScope prof(st, GBHE_PROF_CRT, flops, 0.0);
-  k_fill_int<<<64, 256, 0, st>>>(ea, M + N, -1100);
-  count_launch();
-  const int gA = (M + 31) / 32, gB = (N + 31) / 32;
-  k_op_exponents<<<dim3(gA + gB, (K + 31) / 32), dim3(32, 8), 0, st>>>(oa, ea, ob, eb, gA);
-  count_launch();
-  k_op_residues<<<dim3(gA + gB, Kp / 32), dim3(32, 8), 0, st>>>(oa, ea, PA, ob, eb, PB, gA, Kp);
-  count_launch();
-  rc = cplx ? launch_umma<true>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status)
-            : launch_umma<false>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status);
-  if (rc) return rc;
+  {
+    ProfScope pp(st, GBHE_PROF_CRT_PREP, 0.0, 0.0);
+    k_fill_int<<<64, 256, 0, st>>>(ea, M + N, -1100);
+    count_launch();
+    const int gA = (M + 31) / 32, gB = (N + 31) / 32;
+    k_op_exponents<<<dim3(gA + gB, (K + 31) / 32), dim3(32, 8), 0, st>>>(oa, ea, ob, eb, gA);
+    count_launch();
+    k_op_residues<<<dim3(gA + gB, Kp / 32), dim3(32, 8), 0, st>>>(oa, ea, PA, ob, eb, PB, gA, Kp);
+    count_launch();
+  }
+  {
+    ProfScope pm(st, GBHE_PROF_CRT_MMA, 0.0, 0.0);
+    rc = cplx ? launch_umma<true>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status)
+              : launch_umma<false>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status);
+    if (rc) return rc;
+  }
+  ProfScope pr(st, GBHE_PROF_CRT_REC, 0.0, 0.0);
   const size_t total = out_bytes(M, N, 0) / NMOD / 4;  // four outputs per thread
   k_crt_reconstruct<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(Out, M, N, ea, eb, g, cplx);
   count_launch();

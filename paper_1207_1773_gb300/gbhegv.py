@@ -291,7 +291,8 @@ def trsm_lh(L, X):
     _check("gbhe_trsm_lh", _load().gbhe_trsm_lh(h.h, n, m, _ptr(L), _ld(L), _ptr(X), _ld(X), _stream(L.device)))
 
 
-PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6, "crt": 7}
+PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6, "crt": 7,
+                "crt_prep": 8, "crt_mma": 9, "crt_rec": 10}
 
 
 def launch_count() -> int:
