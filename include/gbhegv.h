@@ -120,7 +120,8 @@ int gbhe_hb2st_sizes(int n, int nb, size_t* v2_elems, size_t* tau2_elems);
  * j -- is H = I - tau v v^H acting on rows s+1+j*nb .. s+nb+j*nb (clipped to
  * n); v (v[0] = 1) is stored at V2 + (s*J + j)*nb and tau at tau2[s*J + j],
  * J = ceil((n-1)/nb).  Q2 is the product of all H in generation order
- * (s major, j minor).  A is not modified. */
+ * (s major, j minor).  A is not modified.  1 <= nb <= 64 (one step's blocks
+ * are held in shared memory). */
 int gbhe_hb2st(gbhe_handle h, int n, int nb, const gbhe_cplx* A, int lda, double* d, double* e,
                gbhe_cplx* V2, gbhe_cplx* tau2, void* stream);
 
@@ -148,7 +149,7 @@ int gbhe_trsm_lh(gbhe_handle h, int n, int m, const gbhe_cplx* L, int ldl, gbhe_
  * eigenpairs il..iu (1-based, inclusive) of A x = lambda B x.  A (lower
  * read) and B (lower read) are overwritten (A by band/V1 data, B by L);
  * w (m) ascending eigenvalues, X (n x m, ldx) B-orthonormal eigenvectors.
- * nb = 0 selects the default band width. */
+ * nb = 0 selects the default band width; 1 <= nb <= 64. */
 int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il,
               int iu, double* w, gbhe_cplx* X, int ldx, void* stream);
 

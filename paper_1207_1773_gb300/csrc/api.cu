@@ -241,7 +241,7 @@ int gbhe_hb2st(gbhe_handle h, int n, int nb, const gbhe_cplx* A, int lda, double
                gbhe_cplx* tau2, void* stream) {
   if (!h) return -1;
   if (n < 0) return -2;
-  if (nb < 1 || nb > 128) return -3;
+  if (nb < 1 || nb > 64) return -3;
   if (n > 0 && !A) return -4;
   if (lda < std::max(1, n)) return -5;
   if (n > 0 && !d) return -6;
@@ -311,7 +311,7 @@ int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B,
   if (!h) return -1;
   if (n < 0) return -2;
   if (nb == 0) nb = default_nb(n);
-  if (nb < 1 || nb > 128) return -3;
+  if (nb < 1 || nb > 64) return -3;
   if (n > 0 && !A) return -4;
   if (lda < std::max(1, n)) return -5;
   if (n > 0 && !B) return -6;

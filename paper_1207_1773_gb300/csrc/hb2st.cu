@@ -22,8 +22,9 @@
 namespace gbhe {
 namespace {
 
-constexpr int HT = 128;
-constexpr int MAXNB = 128;
+constexpr int HT = 256;     // threads per CTA
+constexpr int MAXNB = 64;   // largest band width of the shared-memory chase
+constexpr int LDS = MAXNB + 1;  // smem column pitch (complex elements)
 
 struct ChaseArgs {
   cplx* WB;       // working band, ld = ldb = 2*nb+1:  WB[(r-c) + c*ldb], 0 <= r-c <= 2nb
@@ -37,8 +38,6 @@ struct ChaseArgs {
 __device__ __forceinline__ cplx* bat(const ChaseArgs& a, int r, int c) {
   return a.WB + (size_t)(r - c) + (size_t)c * a.ldb;
 }
-__device__ __forceinline__ cplx ldb_(const cplx* p) { return __ldcg(p); }
-__device__ __forceinline__ void stb_(cplx* p, cplx v) { __stcg(p, v); }
 
 __device__ __forceinline__ cplx warp_sum(cplx v) {
 #pragma unroll
@@ -49,89 +48,118 @@ __device__ __forceinline__ cplx warp_sum(cplx v) {
   return v;
 }
 
-// Reflector from x[0..len) held in smem `x`: on return x = v (v[0] = 1),
-// returns tau, writes beta to *beta.
-__device__ void make_reflector(cplx* x, int len, cplx* tau_out, double* beta_out, cplx* red) {
+// Shared-memory state of one CTA: the step's diagonal block D (full square),
+// its sub-diagonal block E (rows R_j, columns R_{j-1}), the reflectors and
+// reduction scratch.
+struct ChaseSmem {
+  cplx D[MAXNB * LDS];
+  cplx E[MAXNB * LDS];
+  cplx vprev[MAXNB], vcur[MAXNB], y[MAXNB];
+  cplx part[4][MAXNB];
+  cplx red[HT / 32];
+  cplx scal;
+  cplx tau;
+  double beta;
+  int ok;
+};
+
+// Reflector from x[0..len) (in smem): on return x = v (v[0] = 1), S.tau and
+// S.beta set (H^H x = beta e_1, beta real).
+__device__ void make_reflector(ChaseSmem& S, cplx* x, int len) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   double s = 0.0;
   for (int i = 1 + t; i < len; i += HT) s += cabs2(x[i]);
-  cplx sv = warp_sum(mk(s, 0.0));
+  const cplx sv = warp_sum(mk(s, 0.0));
+  if (lane == 0) S.red[warp] = sv;
   __syncthreads();
-  if (lane == 0) red[warp] = sv;
-  __syncthreads();
-  __shared__ cplx sh_scal;
   if (t == 0) {
     double xn2 = 0.0;
-    for (int w = 0; w < HT / 32; ++w) xn2 += red[w].x;
-    cplx al = x[0];
+    for (int w = 0; w < HT / 32; ++w) xn2 += S.red[w].x;
+    const cplx al = x[0];
     if (xn2 == 0.0 && al.y == 0.0) {
-      *tau_out = mk(0.0, 0.0); *beta_out = al.x; sh_scal = mk(0.0, 0.0);
+      S.tau = mk(0.0, 0.0);
+      S.beta = al.x;
+      S.scal = mk(0.0, 0.0);
     } else {
-      double nrm = sqrt(al.x * al.x + al.y * al.y + xn2);
-      double beta = (al.x >= 0.0) ? -nrm : nrm;
-      *beta_out = beta;
-      *tau_out = mk((beta - al.x) / beta, -al.y / beta);
-      sh_scal = cinv(mk(al.x - beta, al.y));
+      const double nrm = sqrt(al.x * al.x + al.y * al.y + xn2);
+      const double beta = (al.x >= 0.0) ? -nrm : nrm;
+      S.beta = beta;
+      S.tau = mk((beta - al.x) / beta, -al.y / beta);
+      S.scal = cinv(mk(al.x - beta, al.y));
     }
   }
   __syncthreads();
-  const cplx sc = sh_scal;
+  const cplx sc = S.scal;
   for (int i = 1 + t; i < len; i += HT) x[i] = cmul(x[i], sc);
-  __syncthreads();
   if (t == 0) x[0] = mk(1.0, 0.0);
   __syncthreads();
 }
 
-// D <- H^H D H for the Hermitian block D = A[a0:a0+L, a0:a0+L] (lower stored).
-__device__ void two_sided(const ChaseArgs& A, int a0, int L, const cplx* v, cplx tau, cplx* p,
-                          cplx* red) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  // p = tau * D v
-  for (int r = t; r < L; r += HT) {
+// out[r] = sum_c M(r, c) x[c], r < R, c < Cn (M column-major, pitch LDS):
+// four threads per row, partial sums combined through S.part.
+__device__ __forceinline__ void smem_gemv(ChaseSmem& S, const cplx* M, int R, int Cn, const cplx* x, cplx* out,
+                                          cplx scale) {
+  const int t = threadIdx.x, r = t & 63, q = t >> 6;
+  if (r < R) {
     cplx acc = mk(0.0, 0.0);
-    for (int c = 0; c < L; ++c) {
-      cplx d = (r >= c) ? ldb_(bat(A, a0 + r, a0 + c)) : cconj(ldb_(bat(A, a0 + c, a0 + r)));
-      if (r == c) d.y = 0.0;
-      cfma(acc, d, v[c]);
-    }
-    p[r] = cmul(tau, acc);
+    for (int c = q; c < Cn; c += 4) cfma(acc, M[c * LDS + r], x[c]);
+    S.part[q][r] = acc;
   }
   __syncthreads();
+  if (t < R) out[t] = cmul(scale, cadd(cadd(S.part[0][t], S.part[1][t]), cadd(S.part[2][t], S.part[3][t])));
+  __syncthreads();
+}
+
+// out[c] = sum_r conj(x[r]) M(r, c), c in [c0, Cn), r < R.
+__device__ __forceinline__ void smem_gemv_h(ChaseSmem& S, const cplx* M, int R, int c0, int Cn, const cplx* x,
+                                            cplx* out, cplx scale) {
+  const int t = threadIdx.x, c = t & 63, q = t >> 6;
+  if (c >= c0 && c < Cn) {
+    cplx acc = mk(0.0, 0.0);
+    for (int r = q; r < R; r += 4) ccfma(acc, x[r], M[c * LDS + r]);
+    S.part[q][c] = acc;
+  }
+  __syncthreads();
+  if (t >= c0 && t < Cn) out[t] = cmul(scale, cadd(cadd(S.part[0][t], S.part[1][t]), cadd(S.part[2][t], S.part[3][t])));
+  __syncthreads();
+}
+
+// D <- H^H D H for the Hermitian L x L block in S.D (full square).
+__device__ void two_sided(ChaseSmem& S, int L, const cplx* v, cplx tau) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  cplx* p = S.y;
+  smem_gemv(S, S.D, L, L, v, p, tau);  // p = tau D v
   // alpha = -1/2 tau (p^H v);  w = p + alpha v
   cplx pv = mk(0.0, 0.0);
   for (int r = t; r < L; r += HT) ccfma(pv, p[r], v[r]);
   pv = warp_sum(pv);
-  if (lane == 0) red[warp] = pv;
+  if (lane == 0) S.red[warp] = pv;
   __syncthreads();
-  __shared__ cplx sh_alpha;
   if (t == 0) {
     cplx s = mk(0.0, 0.0);
-    for (int w = 0; w < HT / 32; ++w) s = cadd(s, red[w]);
-    sh_alpha = cscal(-0.5, cmul(tau, s));
+    for (int w = 0; w < HT / 32; ++w) s = cadd(s, S.red[w]);
+    S.scal = cscal(-0.5, cmul(tau, s));
   }
   __syncthreads();
-  for (int r = t; r < L; r += HT) p[r] = cadd(p[r], cmul(sh_alpha, v[r]));
+  const cplx al = S.scal;
+  for (int r = t; r < L; r += HT) p[r] = cadd(p[r], cmul(al, v[r]));
   __syncthreads();
-  // D -= v w^H + w v^H (lower)
+  // D -= v w^H + w v^H
   for (int i = t; i < L * L; i += HT) {
-    int r = i % L, c = i / L;
-    if (r < c) continue;
-    cplx* q = bat(A, a0 + r, a0 + c);
-    cplx d = ldb_(q);
-    cplx u = cadd(cmulc(v[r], p[c]), cmulc(p[r], v[c]));
-    d = csub(d, u);
+    const int r = i % L, c = i / L;
+    cplx d = csub(S.D[c * LDS + r], cadd(cmulc(v[r], p[c]), cmulc(p[r], v[c])));
     if (r == c) d.y = 0.0;
-    stb_(q, d);
+    S.D[c * LDS + r] = d;
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(HT) k_chase(ChaseArgs A) {
-  __shared__ cplx vprev[MAXNB], vcur[MAXNB], y[MAXNB], p[MAXNB];
-  __shared__ cplx red[HT / 32];
-  __shared__ cplx sh_tau;
-  __shared__ double sh_beta;
-  __shared__ int sh_ok;
+// One CTA per sweep at a time (sweep s on CTA s mod G).  Each step stages its
+// blocks in shared memory: one coalesced read of D (lower, mirrored) and E
+// from the working band, the step's arithmetic on chip, one write back.
+__global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
+  extern __shared__ __align__(16) unsigned char chase_smem_raw[];
+  ChaseSmem& S = *reinterpret_cast<ChaseSmem*>(chase_smem_raw);
   const int t = threadIdx.x, n = A.n, nb = A.nb;
   for (int s = blockIdx.x; s <= n - 2; s += gridDim.x) {
     const int ntask = (n - 1 - s + nb - 1) / nb;
@@ -153,69 +181,79 @@ __global__ void __launch_bounds__(HT) k_chase(ChaseArgs A) {
             }
             __nanosleep(32);
           }
-          sh_ok = ok;
+          S.ok = ok;
         }
         __syncthreads();
-        if (!sh_ok) return;
+        if (!S.ok) return;
       }
       const int a0 = s + 1 + j * nb;
       const int L = min(nb, n - a0);
-      if (j == 0) {
-        for (int i = t; i < L; i += HT) vcur[i] = ldb_(bat(A, a0 + i, s));
-        __syncthreads();
-        make_reflector(vcur, L, &sh_tau, &sh_beta, red);
-        for (int i = t; i < L; i += HT) stb_(bat(A, a0 + i, s), i == 0 ? mk(sh_beta, 0.0) : mk(0.0, 0.0));
-      } else {
-        const int c0 = a0 - nb;  // first column of R_{j-1}
-        // E <- E H_{j-1}:  y = E vprev;  E -= tau_prev y vprev^H
-        for (int r = t; r < L; r += HT) {
-          cplx acc = mk(0.0, 0.0);
-          for (int c = 0; c < Lprev; ++c) cfma(acc, ldb_(bat(A, a0 + r, c0 + c)), vprev[c]);
-          y[r] = cmul(tprev, acc);
+      const int c0 = a0 - nb;  // first column of R_{j-1}
+      // stage D = A[R_j, R_j] (lower read, mirrored) and, for j > 0, E = A[R_j, R_{j-1}]
+      for (int i = t; i < L * L; i += HT) {
+        const int r = i % L, c = i / L;
+        if (r >= c) {
+          cplx d = __ldcg(bat(A, a0 + r, a0 + c));
+          if (r == c) d.y = 0.0;
+          S.D[c * LDS + r] = d;
+          S.D[r * LDS + c] = cconj(d);
         }
-        __syncthreads();
+      }
+      if (j == 0) {
+        for (int i = t; i < L; i += HT) S.vcur[i] = __ldcg(bat(A, a0 + i, s));
+      } else {
         for (int i = t; i < L * Lprev; i += HT) {
-          int r = i % L, c = i / L;
-          cplx* q = bat(A, a0 + r, c0 + c);
-          stb_(q, csub(ldb_(q), cmulc(y[r], vprev[c])));
+          const int r = i % L, c = i / L;
+          S.E[c * LDS + r] = __ldcg(bat(A, a0 + r, c0 + c));
+        }
+      }
+      __syncthreads();
+      if (j == 0) {
+        make_reflector(S, S.vcur, L);
+        for (int i = t; i < L; i += HT) __stcg(bat(A, a0 + i, s), i == 0 ? mk(S.beta, 0.0) : mk(0.0, 0.0));
+      } else {
+        // E <- E H_{j-1}:  y = tau_prev E vprev;  E -= y vprev^H
+        smem_gemv(S, S.E, L, Lprev, S.vprev, S.y, tprev);
+        for (int i = t; i < L * Lprev; i += HT) {
+          const int r = i % L, c = i / L;
+          S.E[c * LDS + r] = csub(S.E[c * LDS + r], cmulc(S.y[r], S.vprev[c]));
         }
         __syncthreads();
         // new reflector from column 0 of E
-        for (int i = t; i < L; i += HT) vcur[i] = ldb_(bat(A, a0 + i, c0));
+        for (int i = t; i < L; i += HT) S.vcur[i] = S.E[i];
         __syncthreads();
-        make_reflector(vcur, L, &sh_tau, &sh_beta, red);
-        for (int i = t; i < L; i += HT) stb_(bat(A, a0 + i, c0), i == 0 ? mk(sh_beta, 0.0) : mk(0.0, 0.0));
-        // E[:, 1:] <- H^H E[:, 1:]:  z_c = v^H E[:, c];  E[:, c] -= conj(tau) v z_c
-        const cplx ct = cconj(sh_tau);
-        for (int c = 1 + t; c < Lprev; c += HT) {
-          cplx acc = mk(0.0, 0.0);
-          for (int r = 0; r < L; ++r) ccfma(acc, vcur[r], ldb_(bat(A, a0 + r, c0 + c)));
-          y[c] = cmul(ct, acc);
-        }
-        __syncthreads();
+        make_reflector(S, S.vcur, L);
+        // E[:, 1:] <- H^H E[:, 1:]:  z_c = conj(tau) v^H E[:, c];  E[:, c] -= v z_c;  E[:, 0] = beta e_1
+        smem_gemv_h(S, S.E, L, 1, Lprev, S.vcur, S.y, cconj(S.tau));
         for (int i = t; i < L * Lprev; i += HT) {
-          int r = i % L, c = i / L;
-          if (c == 0) continue;
-          cplx* q = bat(A, a0 + r, c0 + c);
-          stb_(q, csub(ldb_(q), cmul(vcur[r], y[c])));
+          const int r = i % L, c = i / L;
+          cplx e;
+          if (c == 0) e = (r == 0) ? mk(S.beta, 0.0) : mk(0.0, 0.0);
+          else e = csub(S.E[c * LDS + r], cmul(S.vcur[r], S.y[c]));
+          __stcg(bat(A, a0 + r, c0 + c), e);
         }
-        __syncthreads();
       }
       // store the reflector
       cplx* vout = A.V2 + ((size_t)s * A.J + j) * nb;
-      for (int i = t; i < nb; i += HT) vout[i] = (i < L) ? vcur[i] : mk(0.0, 0.0);
-      if (t == 0) A.tau2[(size_t)s * A.J + j] = sh_tau;
-      // two-sided update of the diagonal block
-      two_sided(A, a0, L, vcur, sh_tau, p, red);
-      // publish progress, keep H_j for the next step
+      for (int i = t; i < nb; i += HT) vout[i] = (i < L) ? S.vcur[i] : mk(0.0, 0.0);
+      if (t == 0) A.tau2[(size_t)s * A.J + j] = S.tau;
+      const cplx tau = S.tau;
+      // two-sided update of the diagonal block, written back (lower)
+      two_sided(S, L, S.vcur, tau);
+      for (int i = t; i < L * L; i += HT) {
+        const int r = i % L, c = i / L;
+        if (r >= c) __stcg(bat(A, a0 + r, a0 + c), S.D[c * LDS + r]);
+      }
+      // keep H_j for the next step
+      for (int i = t; i < L; i += HT) S.vprev[i] = S.vcur[i];
+      tprev = tau;
+      Lprev = L;
+      __syncthreads();
+      // publish progress
       if (t == 0) {
         __threadfence();
         st_release_i(&A.progress[s], j + 1);
       }
-      for (int i = t; i < L; i += HT) vprev[i] = vcur[i];
-      tprev = sh_tau;
-      Lprev = L;
-      __syncthreads();
     }
   }
 }
@@ -265,6 +303,7 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     ca.WB = WB; ca.ldb = ldb; ca.n = n; ca.nb = nb; ca.J = J; ca.V2 = V2; ca.tau2 = tau2;
     ca.progress = prog; ca.st = c.status;
     const int G = std::min(c.num_sms, n - 1);
+    GBHE_CUDA(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChaseSmem)));
     void* args[] = {&ca};
     count_launch();
     double fl = 0.0;
@@ -281,7 +320,7 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     }
     const double by = 16.0 * ((double)n * J * nb + 2.0 * ldb * n);
     ProfScope prof(c.st, GBHE_PROF_CHASE, fl, by);
-    GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_chase, dim3(G), dim3(HT), args, 0, c.st));
+    GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_chase, dim3(G), dim3(HT), args, sizeof(ChaseSmem), c.st));
   }
   k_band_out<<<std::min((n + 255) / 256, 1024), 256, 0, c.st>>>(WB, ldb, n, d, e);
   count_launch();
