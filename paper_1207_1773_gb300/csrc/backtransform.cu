@@ -171,6 +171,7 @@ __global__ void k_q2_desc(int n, int nb, int J, int t, int b_lo, int cnt, const 
   const int r0 = (b + j) * nb + 1, Wh = min(2 * nb - 1, n - r0), W2 = 2 * nb;
   cplx* Wz = Wbuf + (size_t)z * nb * mc;
   CrtDesc d;
+  d.cmap = nullptr;
   d.A = Vg + (size_t)gid * W2 * nb; d.lda = W2;
   d.B = X + (size_t)r0 + (size_t)c0 * ldx; d.ldb = ldx;
   d.C = Wz; d.ldc = nb;

@@ -811,8 +811,11 @@ __global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, i
     const int i0 = bx * CBM + loc % CBM, j = by * CBN + loc / CBM;
     const CrtDesc d = D[z];
     if (i0 >= d.M || j >= d.N) continue;
+    // a column map sends product column j to column cmap[j] of C
+    char* Cj = reinterpret_cast<char*>(d.C) +
+               (d.cmap ? (ptrdiff_t)(d.cmap[j] - j) * d.ldc * (ptrdiff_t)(cplx ? sizeof(double2) : sizeof(double)) : 0);
     crt_store4(tb, Out + tile * NMOD * ncout * OTILE, loc, i0, j, d.M, 0, ea + (size_t)z * maxM,
-               eb[(size_t)z * maxN + j], alpha, beta, cplx, d.C, d.ldc);
+               eb[(size_t)z * maxN + j], alpha, beta, cplx, Cj, d.ldc);
   }
 }
 

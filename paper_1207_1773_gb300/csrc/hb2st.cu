@@ -189,22 +189,29 @@ __global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
       const int a0 = s + 1 + j * nb;
       const int L = min(nb, n - a0);
       const int c0 = a0 - nb;  // first column of R_{j-1}
-      // stage D = A[R_j, R_j] (lower read, mirrored) and, for j > 0, E = A[R_j, R_{j-1}]
-      for (int i = t; i < L * L; i += HT) {
-        const int r = i % L, c = i / L;
-        if (r >= c) {
-          cplx d = __ldcg(bat(A, a0 + r, a0 + c));
-          if (r == c) d.y = 0.0;
-          S.D[c * LDS + r] = d;
-          S.D[r * LDS + c] = cconj(d);
+      // stage D = A[R_j, R_j] (lower read, mirrored) and, for j > 0, E = A[R_j, R_{j-1}]:
+      // every load of a thread is issued before the first shared-memory store
+      {
+        constexpr int PER = MAXNB * MAXNB / HT;
+        cplx dv[PER], ev[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int i = t + k * HT, r = i % MAXNB, c = i / MAXNB;
+          dv[k] = (r < L && c <= r) ? __ldcg(bat(A, a0 + r, a0 + c)) : mk(0.0, 0.0);
+          ev[k] = (j > 0 && r < L && c < Lprev) ? __ldcg(bat(A, a0 + r, c0 + c)) : mk(0.0, 0.0);
         }
-      }
-      if (j == 0) {
-        for (int i = t; i < L; i += HT) S.vcur[i] = __ldcg(bat(A, a0 + i, s));
-      } else {
-        for (int i = t; i < L * Lprev; i += HT) {
-          const int r = i % L, c = i / L;
-          S.E[c * LDS + r] = __ldcg(bat(A, a0 + r, c0 + c));
+        if (j == 0)
+          for (int i = t; i < L; i += HT) S.vcur[i] = __ldcg(bat(A, a0 + i, s));
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int i = t + k * HT, r = i % MAXNB, c = i / MAXNB;
+          if (r < L && c <= r) {
+            cplx d = dv[k];
+            if (r == c) d.y = 0.0;
+            S.D[c * LDS + r] = d;
+            S.D[r * LDS + c] = cconj(d);
+          }
+          if (j > 0 && r < L && c < Lprev) S.E[c * LDS + r] = ev[k];
         }
       }
       __syncthreads();

@@ -64,6 +64,7 @@ struct CrtDesc {
   const void* A;
   const void* B;
   void* C;
+  const int* cmap;  // optional: column j of the product goes to column cmap[j] of C
   int M, N, K, lda, ldb, ldc;
 };
 size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx);

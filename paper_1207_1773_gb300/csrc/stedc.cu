@@ -60,6 +60,7 @@ struct DC {
   double *rtau, *rlam, *zhat;
   int *dfrank, *cpos, *dfpos;
   DGroupDesc* desc;
+  CrtDesc* cdesc;  // the same products for the tensor-core GEMM
   int* st;
 };
 
@@ -575,6 +576,17 @@ __global__ void k_descs(DC a, int lev, int nnodes, int last, int il, int iu, dou
   d1->m = hi - mid; d1->n = nn; d1->k = k - k1; d1->cmap = cmap;
 }
 
+// Descriptors of the tensor-core batched GEMM from the grouped-GEMM ones.
+__global__ void k_crt_descs(const DGroupDesc* in, CrtDesc* out, int cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const DGroupDesc g = in[i];
+  CrtDesc d;
+  d.A = g.A; d.B = g.B; d.C = g.C; d.cmap = g.cmap;
+  d.M = g.m; d.N = g.n; d.K = g.k; d.lda = g.lda; d.ldb = g.ldb; d.ldc = g.ldc;
+  out[i] = d;
+}
+
 // Copy the deflated columns to their final positions.
 __global__ void __launch_bounds__(128) k_copy_defl(DC a, int lev, int last, int il, int iu, double* Zout,
                                                    int ldz) {
@@ -617,6 +629,7 @@ size_t stedc_ws_bytes(int n) {
   b += 20 * nn * sizeof(int);                      // per-index ints
   b += (nn / LS + 2) * 8 * sizeof(int);            // counters
   b += (nn / LS + 2) * 2 * sizeof(DGroupDesc);     // descriptors
+  b += (nn / LS + 2) * 2 * sizeof(CrtDesc);
   b += 64 * 256;
   return b;
 }
@@ -646,6 +659,7 @@ int stedc_run(Ctx& c, int n, const double* d, const double* e, int il, int iu, d
   a.dfrank = ar.take<int>(nn); a.cpos = ar.take<int>(nn); a.dfpos = ar.take<int>(nn);
   int* cmap_last = ar.take<int>(nn);
   a.desc = ar.take<DGroupDesc>((size_t)(a.nleaf + 1) * 2);
+  a.cdesc = ar.take<CrtDesc>((size_t)(a.nleaf + 1) * 2);
   a.st = c.status;
   if (!ar.ok() || !a.desc) { ar.off = save; return GBHE_EWORKSPACE; }
 
@@ -686,7 +700,19 @@ int stedc_run(Ctx& c, int n, const double* d, const double* e, int il, int iu, d
     k_descs<<<(nnodes + 127) / 128, 128, 0, c.st>>>(a, lev, nnodes, last, il, iu, Zout, ldz, cmap_last);
     count_launch();
     GBHE_CUDA(cudaGetLastError());
-    int rc = dgemm_grouped(c.st, a.desc, 2 * nnodes, span, span, 1.0, 0.0);
+    // merge products: Z(rows of the node) = Zt Q on the tensor-core engine
+    // when its workspace holds the level's batch, else on the FP64 pipe
+    const int maxm = std::min(span, (1 << (lev - 1)) * LS);
+    int rc;
+    if (c.engine == GBHE_ENGINE_CRT && c.crt_ws && span >= 256 &&
+        crt_batched_ws_bytes(2 * nnodes, maxm, span, span, 0) <= c.crt_ws_bytes) {
+      k_crt_descs<<<(2 * nnodes + 127) / 128, 128, 0, c.st>>>(a.desc, a.cdesc, 2 * nnodes);
+      count_launch();
+      rc = crt_gemm_batched(c.st, OP_N, OP_N, mk(1.0, 0.0), mk(0.0, 0.0), 0, a.cdesc, 2 * nnodes, maxm, span, span,
+                            c.crt_ws, c.crt_ws_bytes, c.status);
+    } else {
+      rc = dgemm_grouped(c.st, a.desc, 2 * nnodes, span, span, 1.0, 0.0);
+    }
     if (rc) { ar.off = save; return rc; }
     k_copy_defl<<<n, 128, 0, c.st>>>(a, lev, last, il, iu, Zout, ldz);
     count_launch();
