@@ -37,10 +37,10 @@ sys.path.insert(0, ROOT)
 METRIC = "generalized solve time (s) & GFLOP/s at n=10k complex128 vs one-stage on same GPU"
 UNIT = "GFLOP/s"
 CPU_SAMPLE_N = 2048
-# FP16 mma.sync m16n8k16 (f32 accumulate) throughput measured on this GPU with a
-# register-only saturating kernel (all SMs, 64 warps/SM): the ceiling of the
-# legacy tensor-core path the CRT GEMM uses.
-LEGACY_HMMA_TFLOPS = 603.0
+# Tensor flops of the CRT GEMM per FP64-equivalent flop: 16 moduli, and per
+# complex multiply-add (8 real flops) four real FP16 products of 2 flops each
+# (real operands: one product per real multiply-add) -> 16 x.
+CRT_TENSOR_PER_FP64 = 16.0
 
 
 def _load_peaks():
@@ -319,18 +319,21 @@ def run_ours(args):
     pd = prof[dom]
     roof = None
     if dom == "crt":
-        # FP64-exact complex products on FP16 mma.sync: 16 moduli x 3 Karatsuba
-        # products x 2 flops = 96 m n k tensor flops per 8 m n k FP64 flops.
+        # the dominant kernel is the residue-product kernel k_crt_umma
+        # (tcgen05.mma kind::f16): algorithmic tensor flops = 16 x the
+        # FP64-equivalent flops of the products it serves, over its own time
+        pm = prof["crt_mma"]
+        ach = CRT_TENSOR_PER_FP64 * pm["flops"] / (pm["ms"] * 1e-3) / 1e12
         fp64eq = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
-        ach = 12.0 * fp64eq
         peak = PEAKS.get("bf16_tflops")
-        roof = {"kernel": "CRT GEMM (k_op_exponents, k_op_residues, k_crt_mma FP16 mma.sync m16n8k16, "
-                          "k_crt_reconstruct)", "bound": "tensor", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": (ach / peak) if peak else None, "traffic": None,
-                "fp64_equivalent_tflops": fp64eq, "fp64_equivalent_frac_of_fp64_peak": fp64eq / dmma_peak,
-                "peak_source": "measured dense bf16 (MEASURED_PEAKS.json, same rate as fp16); the legacy "
-                               "mma.sync path this kernel uses measured %.0f TFLOP/s" % LEGACY_HMMA_TFLOPS,
-                "launches": pd["launches"], "ms": pd["ms"]}
+        roof = {"kernel": "k_crt_umma (tcgen05.mma kind::f16, FP32 accumulators in TMEM)", "bound": "tensor",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": (ach / peak) if peak else None,
+                "traffic": None,
+                "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json; fp16 runs at the bf16 rate)",
+                "launches": pm["launches"], "ms": pm["ms"],
+                "crt_gemm_fp64_equivalent_tflops": fp64eq,
+                "crt_gemm_fp64_equivalent_frac_of_fp64_peak": fp64eq / dmma_peak,
+                "crt_gemm_phase_ms": {k: round(prof[k]["ms"], 1) for k in ("crt_prep", "crt_mma", "crt_rec")}}
     elif dom in ("zgemm", "dgemm"):
         ach = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
         roof = {"kernel": "k_gemm<complex> (DMMA mma.sync m16n8k4 f64)" if dom == "zgemm" else "k_gemm<real>",

@@ -282,11 +282,15 @@ static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const c
       if (cnt == 0) continue;
       k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, t, b_lo, cnt, Vg, Ug, X, ldx, c0, mcc, Wbuf, D1, D2);
       count_launch();
+      double gfl = 0.0;  // each of the two products: 8 nb mcc Wh per diamond
+      if (prof_on())
+        for (int z = 0; z < cnt; ++z)
+          gfl += 8.0 * nb * mcc * std::min(2 * nb - 1, n - ((b_lo + z + t - 2 * (J - 1 - (b_lo + z))) * nb + 1));
       rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, nb, mcc, W2 - 1, c.crt_ws,
-                            c.crt_ws_bytes, c.status);
+                            c.crt_ws_bytes, c.status, gfl);
       if (!rc)
         rc = crt_gemm_batched(c.st, OP_N, OP_N, mk(-1, 0), mk(1, 0), 1, D2, cnt, W2 - 1, mcc, nb, c.crt_ws,
-                              c.crt_ws_bytes, c.status);
+                              c.crt_ws_bytes, c.status, gfl);
     }
   }
   ar.off = save;

@@ -596,6 +596,211 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CF::COLS));
 }
 
+// Warp-specialised form for products whose moduli are each one exact chunk
+// (Kp <= KC_TERMS: the K <= 256 updates of the blocked factorisations, the
+// panel updates and the Q2 block reflectors).  Warps 0-3 stage operands with
+// cp.async and thread 0 issues the MMAs; warps 4-7 drain the TMEM buffer of
+// the previous modulus (reduce, stage bytes, write the residue tile) while
+// the tensor cores work on the next one.  Handshakes: per stage "empty"
+// (MMA completion), per TMEM buffer "full" (MMA completion) and "drained"
+// (the 128 epilogue threads).  Grid and arguments as for k_crt_umma.
+constexpr int WS_STAGES = 4;
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// Bounded wait that gives up at once after any thread of the CTA recorded a timeout.
+__device__ __forceinline__ void mbar_wait_cta(unsigned bar, unsigned parity, volatile int* sabort, int* status) {
+  if (*sabort) return;
+  if (!mbar_wait(bar, parity)) {
+    *sabort = 1;
+    if (status) set_err_once(status, GBHE_ETIMEOUT);
+  }
+}
+
+template <bool CPLX>
+struct WsCfg {
+  static constexpr int NC = UCfg<CPLX>::NC;
+  static constexpr int STB = UCfg<CPLX>::STB;
+  static constexpr int STILE = NC * UBN * OPITCH;
+  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 2 * (size_t)STILE + 8 * (WS_STAGES + 4) + 16;
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma_ws(const __half* PA, const __half* PB, int M, int N,
+                                                            int Kp, unsigned char* Out, const CrtDesc* D, int maxM,
+                                                            int maxN, int lower, int mpc, int* status) {
+  using CF = UCfg<CPLX>;
+  using WF = WsCfg<CPLX>;
+  constexpr int NC = CF::NC;
+  constexpr int STB = CF::STB;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* stile0 = smem_raw + WS_STAGES * STB;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile0 + 2 * WF::STILE);
+  // bars: [0, S) stage empty, S + b accumulator full, S + 2 + b accumulator drained
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + WS_STAGES + 4);
+  volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
+  const int TN = (maxN + CBN - 1) / CBN;
+  const int ngrp = NMOD / mpc;
+  const int entry = blockIdx.z / ngrp, grp = blockIdx.z % ngrp;
+  int bx, by;
+  {
+    const int pid = blockIdx.x, GM = 8;
+    const int first = (pid / (GM * TN2)) * GM, gm = min(TM - first, GM);
+    bx = first + (pid % (GM * TN2)) % gm;
+    by = (pid % (GM * TN2)) / gm;
+  }
+  if (D) {
+    M = D[entry].M;
+    N = D[entry].N;
+    PA += (size_t)entry * NMOD * NC * maxM * Kp;
+    PB += (size_t)entry * NMOD * NC * maxN * Kp;
+    Out += (size_t)entry * TM * TN * NMOD * NC * OTILE;
+  }
+  const int m0 = bx * UBM, n0 = by * UBN;
+  if (m0 >= M || n0 >= N) return;
+  if (lower && m0 + UBM - 1 < n0) return;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int l0 = grp * mpc;
+  const size_t planeA = (size_t)M * Kp, planeB = (size_t)N * Kp;
+
+  if (t == 0) {
+    for (int i = 0; i < WS_STAGES + 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_addr(bars + WS_STAGES + 2 + i)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *sabort = 0;
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(CF::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tslot;
+  const int ktiles = Kp / UBK;
+  const int iters = mpc * ktiles;
+
+  if (w < 4) {
+    // ---------------- producers (128 threads); thread 0 also issues the MMAs
+    const unsigned idesc = (1u << 4) | ((unsigned)(UBN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
+    const unsigned idesc_negA = idesc | (1u << 13);
+    auto load = [&](int it) {
+      unsigned char* sA = smem_raw + (it % WS_STAGES) * STB;
+      unsigned char* sB = sA + NC * U_APL;
+      const int l = l0 + it / ktiles, k0 = (it % ktiles) * UBK;
+      const __half* Al = PA + (size_t)l * NC * planeA;
+      const __half* Bl = PB + (size_t)l * NC * planeB;
+#pragma unroll
+      for (int i = t; i < NC * UBM * 4; i += 128) {
+        const int c = i / (UBM * 4), rem = i % (UBM * 4), r = rem >> 2, kg = rem & 3;
+        const bool ok = (m0 + r) < M;
+        const __half* src = Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + kg * 8;
+        cp16(sA + c * U_APL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
+      }
+#pragma unroll
+      for (int i = t; i < NC * UBN * 4; i += 128) {
+        const int c = i / (UBN * 4), rem = i % (UBN * 4), r = rem >> 2, kg = rem & 3;
+        const bool ok = (n0 + r) < N;
+        const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + kg * 8;
+        cp16(sB + c * U_BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
+      }
+    };
+#pragma unroll
+    for (int s = 0; s < WS_STAGES - 1; ++s) {
+      if (s < iters) load(s);
+      cp_commit();
+    }
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % WS_STAGES;
+      const int li = it / ktiles, kt = it % ktiles, b = li & 1;
+      cp_wait<WS_STAGES - 2>();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync(1, 128);
+      if (t == 0) {
+        // buffer b must have been drained by the epilogue of modulus li - 2
+        if (kt == 0 && li >= 2)
+          mbar_wait_cta(smem_addr(bars + WS_STAGES + 2 + b), (unsigned)((li - 2) >> 1) & 1u, sabort, status);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned dbuf = tmem + (unsigned)b * CF::BUFC;
+        const unsigned sA = smem_addr(smem_raw + s * STB), sB = sA + NC * U_APL;
+#pragma unroll
+        for (int kk = 0; kk < UBK / 16; ++kk) {
+          const unsigned first = (kt == 0 && kk == 0) ? 0u : 1u;
+          const unsigned long long ar = umma_sdesc(sA + kk * 256, 128, 512);
+          const unsigned long long br = umma_sdesc(sB + kk * 256, 128, 512);
+          umma_f16(dbuf, ar, br, idesc, first);
+          if constexpr (CPLX) {
+            const unsigned long long ai = umma_sdesc(sA + U_APL + kk * 256, 128, 512);
+            const unsigned long long bi = umma_sdesc(sB + U_BPL + kk * 256, 128, 512);
+            umma_f16(dbuf, ai, bi, idesc_negA, 1u);
+            umma_f16(dbuf + UBN, ar, bi, idesc, first);
+            umma_f16(dbuf + UBN, ai, br, idesc, 1u);
+          }
+        }
+        umma_commit(smem_addr(bars + s));
+        if (kt == ktiles - 1) umma_commit(smem_addr(bars + WS_STAGES + b));
+      }
+      if (it + WS_STAGES - 1 < iters) {
+        if (it >= 1)
+          mbar_wait_cta(smem_addr(bars + (it - 1) % WS_STAGES), (unsigned)((it - 1) / WS_STAGES) & 1u, sabort,
+                        status);
+        load(it + WS_STAGES - 1);
+      }
+      cp_commit();
+    }
+    cp_wait<0>();
+  } else {
+    // ---------------- epilogue (128 threads): row 32 q + lane of the tile
+    const int q = w & 3, il = 32 * q + lane, et = t - 128;
+    for (int li = 0; li < mpc; ++li) {
+      const int b = li & 1, l = l0 + li;
+      unsigned char* stile = stile0 + (li & 1) * WF::STILE;
+      mbar_wait_cta(smem_addr(bars + WS_STAGES + b), (unsigned)(li >> 1) & 1u, sabort, status);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const float p = (float)c_p[l], pinv = c_pinv[l];
+      const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC;
+#pragma unroll 1
+      for (int sl = 0; sl < UBN / 16; ++sl) {
+        float P[NC][16];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int x = 0; x < 16; ++x) {
+            float v = red_sym(P[c][x], p, pinv);  // |v| <= p/2 + 1
+            if (v < 0.f) v += p;                  // [0, p)
+            stile[(c * UBN + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
+          }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_addr(bars + WS_STAGES + 2 + b));  // buffer b may be overwritten
+      named_sync(2, 128);
+      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
+      for (int i = et; i < NC * ncol * nu; i += 128) {
+        const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, uu = rem % nu;
+        const int tile = (2 * by + jl / CBN) * TM + bx;
+        unsigned char* dst = Out + ((size_t)tile * NMOD + l) * NC * OTILE;
+        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * UBN + jl) * OPITCH + uu * 16);
+        *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + (jl % CBN)) * CBM + uu * 16) = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CF::COLS));
+}
+
 // ------------------------------------------------------------------ reconstruction
 // value of the 160-bit two's complement integer D times 2^sc, rounded to double
 __device__ __forceinline__ double int160_to_double(unsigned (&D)[5], int sc) {
@@ -830,8 +1035,12 @@ int umma_prepare(int* nsm_out) {
   static bool ready = false;
   static int nsm = 0;
   if (!ready) {
-    GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)UCfg<CPLX>::SMEM));
+    if (ONE)
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma_ws<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)WsCfg<CPLX>::SMEM));
+    else
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)UCfg<CPLX>::SMEM));
     int dev = 0;
     GBHE_CUDA(cudaGetDevice(&dev));
     GBHE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -844,7 +1053,6 @@ int umma_prepare(int* nsm_out) {
 template <bool CPLX>
 int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
                 const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
-  const size_t smem = UCfg<CPLX>::SMEM;
   const bool one = Kp <= UCfg<CPLX>::KC_TERMS;
   int nsm = 0;
   int rc = one ? umma_prepare<CPLX, true>(&nsm) : umma_prepare<CPLX, false>(&nsm);
@@ -856,9 +1064,11 @@ int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int 
   while (mpc > 1 && tiles * (NMOD / mpc) < 2L * nsm) mpc /= 2;
   dim3 grid(TM * TN2, 1, (NMOD / mpc) * nbatch);
   if (one)
-    k_crt_umma<CPLX, true><<<grid, UTHREADS, smem, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc, status);
+    k_crt_umma_ws<CPLX><<<grid, UTHREADS, WsCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc,
+                                                                    status);
   else
-    k_crt_umma<CPLX, false><<<grid, UTHREADS, smem, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc, status);
+    k_crt_umma<CPLX, false><<<grid, UTHREADS, UCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
+                                                                       mpc, status);
   count_launch();
   return 0;
 }
@@ -899,7 +1109,7 @@ size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) 
 }
 
 int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, int cplx_flag, const CrtDesc* D,
-                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes, int* status) {
+                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes, int* status, double flops) {
   if (nbatch <= 0 || maxM <= 0 || maxN <= 0 || maxK <= 0) return 0;
   if (maxK > KMAX || nbatch > 65535 / NMOD) return GBHE_EWORKSPACE;
   if (crt_batched_ws_bytes(nbatch, maxM, maxN, maxK, cplx_flag) > ws_bytes) return GBHE_EWORKSPACE;
@@ -914,7 +1124,7 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)nbatch * out_bytes(maxM, maxN, cplx_flag)));
   int* ea = reinterpret_cast<int*>(take((size_t)nbatch * (maxM + maxN) * sizeof(int)));
   int* eb = ea + (size_t)nbatch * maxM;
-  ProfScope prof(st, GBHE_PROF_CRT, 0.0, 0.0);
+  ProfScope prof(st, GBHE_PROF_CRT, flops, 0.0);
   {
     ProfScope pp(st, GBHE_PROF_CRT_PREP, 0.0, 0.0);
     k_fill_int_batched<<<256, 256, 0, st>>>(ea, (size_t)nbatch * (maxM + maxN), -1100);
@@ -928,7 +1138,7 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
     count_launch();
   }
   {
-    ProfScope pm(st, GBHE_PROF_CRT_MMA, 0.0, 0.0);
+    ProfScope pm(st, GBHE_PROF_CRT_MMA, flops, 0.0);
     rc = cplx_flag ? launch_umma<true>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status)
                    : launch_umma<false>(st, PA, PB, maxM, maxN, Kp, Out, D, maxM, maxN, 0, nbatch, status);
     if (rc) return rc;
@@ -1035,7 +1245,7 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
     count_launch();
   }
   {
-    ProfScope pm(st, GBHE_PROF_CRT_MMA, 0.0, 0.0);
+    ProfScope pm(st, GBHE_PROF_CRT_MMA, flops, 0.0);
     rc = cplx ? launch_umma<true>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status)
               : launch_umma<false>(st, PA, PB, M, N, Kp, Out, nullptr, M, N, g.lower_only, 1, status);
     if (rc) return rc;

@@ -68,8 +68,11 @@ struct CrtDesc {
   int M, N, K, lda, ldb, ldc;
 };
 size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx);
+// `flops` (FP64-equivalent, for the profiler only) is the caller's count of
+// the batch's work; the entries' sizes live on the device.
 int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, int cplx_flag, const CrtDesc* d_desc,
-                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes, int* status);
+                     int nbatch, int maxM, int maxN, int maxK, void* ws, size_t ws_bytes, int* status,
+                     double flops = 0.0);
 
 size_t dense_ws_bytes(int n);
 int potrf_run(Ctx& c, int n, cplx* B, int ldb);
