@@ -599,12 +599,14 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
 // Warp-specialised form for products whose moduli are each one exact chunk
 // (Kp <= KC_TERMS: the K <= 256 updates of the blocked factorisations, the
 // panel updates and the Q2 block reflectors).  Warps 0-3 stage operands with
-// cp.async and thread 0 issues the MMAs; warps 4-7 drain the TMEM buffer of
-// the previous modulus (reduce, stage bytes, write the residue tile) while
-// the tensor cores work on the next one.  Handshakes: per stage "empty"
-// (MMA completion), per TMEM buffer "full" (MMA completion) and "drained"
-// (the 128 epilogue threads).  Grid and arguments as for k_crt_umma.
+// cp.async and thread 0 issues the MMAs; warps 4-11 (two per TMEM lane
+// quarter, 64 columns each) drain the TMEM buffer of the previous modulus
+// (reduce, stage bytes, write the residue tile) while the tensor cores work
+// on the next one.  Handshakes: per stage "empty" (MMA completion), per TMEM
+// buffer "full" (MMA completion) and "drained" (the 256 epilogue threads).
+// Grid and arguments as for k_crt_umma, 384 threads.
 constexpr int WS_STAGES = 4;
+constexpr int WS_THREADS = 384, WS_EPI = 256;
 
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
@@ -630,7 +632,7 @@ struct WsCfg {
 };
 
 template <bool CPLX>
-__global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma_ws(const __half* PA, const __half* PB, int M, int N,
+__global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA, const __half* PB, int M, int N,
                                                             int Kp, unsigned char* Out, const CrtDesc* D, int maxM,
                                                             int maxN, int lower, int mpc, int* status) {
   using CF = UCfg<CPLX>;
@@ -673,7 +675,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma_ws(const __half* PA, c
     for (int i = 0; i < WS_STAGES + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
     for (int i = 0; i < 2; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_addr(bars + WS_STAGES + 2 + i)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + WS_STAGES + 2 + i)), "r"(WS_EPI));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sabort = 0;
   }
@@ -759,17 +761,17 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma_ws(const __half* PA, c
     }
     cp_wait<0>();
   } else {
-    // ---------------- epilogue (128 threads): row 32 q + lane of the tile
-    const int q = w & 3, il = 32 * q + lane, et = t - 128;
+    // ---------------- epilogue (256 threads): row 32 q + lane, columns 64 hh .. 64 hh + 63
+    const int q = w & 3, hh = (w - 4) >> 2, il = 32 * q + lane, et = t - 128;
     for (int li = 0; li < mpc; ++li) {
       const int b = li & 1, l = l0 + li;
       unsigned char* stile = stile0 + (li & 1) * WF::STILE;
       mbar_wait_cta(smem_addr(bars + WS_STAGES + b), (unsigned)(li >> 1) & 1u, sabort, status);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float p = (float)c_p[l], pinv = c_pinv[l];
-      const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC;
+      const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(64 * hh);
 #pragma unroll 1
-      for (int sl = 0; sl < UBN / 16; ++sl) {
+      for (int sl = 0; sl < 4; ++sl) {
         float P[NC][16];
 #pragma unroll
         for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
@@ -780,14 +782,14 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma_ws(const __half* PA, c
           for (int x = 0; x < 16; ++x) {
             float v = red_sym(P[c][x], p, pinv);  // |v| <= p/2 + 1
             if (v < 0.f) v += p;                  // [0, p)
-            stile[(c * UBN + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
+            stile[(c * UBN + 64 * hh + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
           }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_addr(bars + WS_STAGES + 2 + b));  // buffer b may be overwritten
-      named_sync(2, 128);
+      named_sync(2, WS_EPI);
       const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
-      for (int i = et; i < NC * ncol * nu; i += 128) {
+      for (int i = et; i < NC * ncol * nu; i += WS_EPI) {
         const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, uu = rem % nu;
         const int tile = (2 * by + jl / CBN) * TM + bx;
         unsigned char* dst = Out + ((size_t)tile * NMOD + l) * NC * OTILE;
@@ -882,27 +884,13 @@ __device__ __forceinline__ void combine160(unsigned (&D)[5], unsigned long long 
   D[4] = (unsigned)(t >> 32);
 }
 
-__device__ __forceinline__ double crt_value(const volatile CrtTables* tb, const unsigned (&w)[NMOD], int sh, int sc) {
-  // S = sum_l c_l W_l as four independent 64-bit word sums (each term < 2^40,
-  // sixteen terms < 2^44), carries propagated once at the end
-  unsigned long long X0 = 0, X1 = 0, X2 = 0, X3 = 0;
-  float F0 = 0.f, F1 = 0.f;
-#pragma unroll
-  for (int l = 0; l < NMOD; ++l) {
-    const unsigned c = (w[l] >> sh) & 0xFFu;
-    X0 += (unsigned long long)c * tb->W[l][0];
-    X1 += (unsigned long long)c * tb->W[l][1];
-    X2 += (unsigned long long)c * tb->W[l][2];
-    X3 += (unsigned long long)c * tb->W[l][3];
-    if (l & 1) F1 = fmaf((float)c, tb->frac[l], F1);
-    else F0 = fmaf((float)c, tb->frac[l], F0);
-  }
+// Double value of (S - q M) 2^sc for the CRT sum held as four 64-bit word sums.
+__device__ __forceinline__ double crt_finish(const unsigned long long (&X)[4], float F, const unsigned (&Mw)[4], int sc) {
   unsigned S[5], qM[5];
-  combine160(S, X0, X1, X2, X3);
-  const unsigned q = (unsigned)rintf(F0 + F1);  // < 2^12
-  combine160(qM, (unsigned long long)q * tb->M[0], (unsigned long long)q * tb->M[1],
-             (unsigned long long)q * tb->M[2], (unsigned long long)q * tb->M[3]);
-  // D = S - q M
+  combine160(S, X[0], X[1], X[2], X[3]);
+  const unsigned q = (unsigned)rintf(F);  // < 2^12
+  combine160(qM, (unsigned long long)q * Mw[0], (unsigned long long)q * Mw[1], (unsigned long long)q * Mw[2],
+             (unsigned long long)q * Mw[3]);
   unsigned D[5];
   unsigned borrow = 0;
 #pragma unroll
@@ -916,50 +904,65 @@ __device__ __forceinline__ double crt_value(const volatile CrtTables* tb, const 
 
 // Reconstruct four consecutive rows i0..i0+3 of column j of one output tile
 // (tile base `T` in the tile-major residue layout, offset `loc` inside it)
-// and update C.
+// and update C.  For every modulus the table words W_l are read once and
+// applied to all eight values (four rows, real and imaginary parts): the
+// CRT sum of each value is kept as four independent 64-bit word sums (each
+// term < 2^40, sixteen terms < 2^44), carries propagated once at the end.
+template <bool CPLX>
 __device__ __forceinline__ void crt_store4(const volatile CrtTables* tb, const unsigned char* T, int loc, int i0,
-                                           int j, int M, int lower,
-                                           const int* ea, int ebj, double2 alpha, double2 beta, int cplx, void* Cv,
-                                           int ldc) {
-  const int ncout = cplx ? 2 : 1;
+                                           int j, int M, int lower, const int* ea, int ebj, double2 alpha,
+                                           double2 beta, void* Cv, int ldc) {
+  constexpr int NCOUT = CPLX ? 2 : 1;
   const bool beta0 = (beta.x == 0.0 && beta.y == 0.0);
   const bool beta1 = (beta.x == 1.0 && beta.y == 0.0);
   const bool alpha1 = (alpha.x == 1.0 && alpha.y == 0.0);
   const bool alpham1 = (alpha.x == -1.0 && alpha.y == 0.0);
-  // real parts of the four rows, then imaginary parts: one set of residue
-  // words live at a time
-  double vr[4], vi[4];
-  int sc[4];
+  unsigned w[NCOUT][NMOD];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) sc[r] = (i0 + r < M) ? ea[i0 + r] + ebj - 104 : 0;
-  {
-    unsigned w[NMOD];
+  for (int l = 0; l < NMOD; ++l)
 #pragma unroll
-    for (int l = 0; l < NMOD; ++l) w[l] = *reinterpret_cast<const unsigned*>(T + (size_t)(l * ncout) * OTILE + loc);
+    for (int c = 0; c < NCOUT; ++c)
+      w[c][l] = *reinterpret_cast<const unsigned*>(T + (size_t)(l * NCOUT + c) * OTILE + loc);
+  unsigned long long X[NCOUT][4][4];
+  float F[NCOUT][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) vr[r] = crt_value(tb, w, 8 * r, sc[r]);
+  for (int c = 0; c < NCOUT; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      F[c][r] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) X[c][r][k] = 0ull;
+    }
+#pragma unroll
+  for (int l = 0; l < NMOD; ++l) {
+    const unsigned W0 = tb->W[l][0], W1 = tb->W[l][1], W2 = tb->W[l][2], W3 = tb->W[l][3];
+    const float fr = tb->frac[l];
+#pragma unroll
+    for (int c = 0; c < NCOUT; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const unsigned cv = (w[c][l] >> (8 * r)) & 0xFFu;
+        X[c][r][0] += (unsigned long long)cv * W0;
+        X[c][r][1] += (unsigned long long)cv * W1;
+        X[c][r][2] += (unsigned long long)cv * W2;
+        X[c][r][3] += (unsigned long long)cv * W3;
+        F[c][r] = fmaf((float)cv, fr, F[c][r]);
+      }
   }
-  if (cplx) {
-    unsigned w[NMOD];
-#pragma unroll
-    for (int l = 0; l < NMOD; ++l)
-      w[l] = *reinterpret_cast<const unsigned*>(T + (size_t)(l * ncout + 1) * OTILE + loc);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) vi[r] = crt_value(tb, w, 8 * r, sc[r]);
-  } else {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) vi[r] = 0.0;
-  }
+  const unsigned Mw[4] = {tb->M[0], tb->M[1], tb->M[2], tb->M[3]};
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int i = i0 + r;
     if (i >= M || (lower && i < j)) continue;
+    const int sc = ea[i] + ebj - 104;
+    const double vr = crt_finish(X[0][r], F[0][r], Mw, sc);
+    const double vi = CPLX ? crt_finish(X[NCOUT - 1][r], F[NCOUT - 1][r], Mw, sc) : 0.0;
     double2 out;
-    if (alpha1) out = make_double2(vr[r], vi[r]);
-    else if (alpham1) out = make_double2(-vr[r], -vi[r]);
-    else out = cmul(alpha, make_double2(vr[r], vi[r]));
+    if (alpha1) out = make_double2(vr, vi);
+    else if (alpham1) out = make_double2(-vr, -vi);
+    else out = cmul(alpha, make_double2(vr, vi));
     const size_t ci = (size_t)i + (size_t)j * ldc;
-    if (cplx) {
+    if (CPLX) {
       double2* C = reinterpret_cast<double2*>(Cv);
       if (beta1) out = cadd(out, C[ci]);
       else if (!beta0) out = cadd(out, cmul(beta, C[ci]));
@@ -991,8 +994,9 @@ __global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const 
     const int i0 = bx * CBM + loc % CBM, j = by * CBN + loc / CBM;
     if (i0 >= M || j >= N) continue;
     if (g.lower_only && i0 + 3 < j) continue;
-    crt_store4(tb, Out + tile * NMOD * ncout * OTILE, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, cplx,
-               g.C, g.ldc);
+    const unsigned char* T = Out + tile * NMOD * ncout * OTILE;
+    if (cplx) crt_store4<true>(tb, T, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, g.C, g.ldc);
+    else crt_store4<false>(tb, T, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, g.C, g.ldc);
   }
 }
 
@@ -1019,8 +1023,13 @@ __global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, i
     // a column map sends product column j to column cmap[j] of C
     char* Cj = reinterpret_cast<char*>(d.C) +
                (d.cmap ? (ptrdiff_t)(d.cmap[j] - j) * d.ldc * (ptrdiff_t)(cplx ? sizeof(double2) : sizeof(double)) : 0);
-    crt_store4(tb, Out + tile * NMOD * ncout * OTILE, loc, i0, j, d.M, 0, ea + (size_t)z * maxM,
-               eb[(size_t)z * maxN + j], alpha, beta, cplx, Cj, d.ldc);
+    const unsigned char* T = Out + tile * NMOD * ncout * OTILE;
+    if (cplx)
+      crt_store4<true>(tb, T, loc, i0, j, d.M, 0, ea + (size_t)z * maxM, eb[(size_t)z * maxN + j], alpha, beta, Cj,
+                       d.ldc);
+    else
+      crt_store4<false>(tb, T, loc, i0, j, d.M, 0, ea + (size_t)z * maxM, eb[(size_t)z * maxN + j], alpha, beta, Cj,
+                        d.ldc);
   }
 }
 
@@ -1064,8 +1073,8 @@ int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int 
   while (mpc > 1 && tiles * (NMOD / mpc) < 2L * nsm) mpc /= 2;
   dim3 grid(TM * TN2, 1, (NMOD / mpc) * nbatch);
   if (one)
-    k_crt_umma_ws<CPLX><<<grid, UTHREADS, WsCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, mpc,
-                                                                    status);
+    k_crt_umma_ws<CPLX><<<grid, WS_THREADS, WsCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
+                                                                      mpc, status);
   else
     k_crt_umma<CPLX, false><<<grid, UTHREADS, UCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
                                                                        mpc, status);
