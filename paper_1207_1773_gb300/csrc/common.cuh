@@ -90,9 +90,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
       __threadfence();
       atomicAdd(&bar[1], 1u);
     } else {
+      // the shared status word is looked at only every 64 polls, so that the
+      // waiting CTAs do not crowd the L2 slice that holds it
       const unsigned long long t0 = gtimer();
+      unsigned polls = 0;
       while (ld_acquire(&bar[1]) == gen) {
-        if (gtimer() - t0 > GBHE_WAIT_NS || ld_acquire_i(&st[ST_ERR]) != 0) {
+        if ((++polls & 63) == 0 && (gtimer() - t0 > GBHE_WAIT_NS || ld_acquire_i(&st[ST_ERR]) != 0)) {
           set_err_once(st, GBHE_ETIMEOUT);
           ok = 0;
           break;

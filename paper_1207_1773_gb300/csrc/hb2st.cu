@@ -31,9 +31,10 @@ struct ChaseArgs {
   int ldb, n, nb, J;
   cplx* V2;       // (s*J + j)*nb
   cplx* tau2;     // s*J + j
-  int* progress;  // n
+  int* progress;  // n counters, PSTRIDE ints apart (one 128-byte line each)
   int* st;
 };
+constexpr int PSTRIDE = 32;
 
 __device__ __forceinline__ cplx* bat(const ChaseArgs& a, int r, int c) {
   return a.WB + (size_t)(r - c) + (size_t)c * a.ldb;
@@ -170,16 +171,20 @@ __global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
       // wait for sweep s-1 to finish step j+1
       if (s > 0) {
         if (t == 0) {
+          // poll sweep s-1's counter (its own cache line) with a growing pause;
+          // the shared status word is looked at only every 64 polls
           const int need = min(j + 2, ntask_prev);
           const unsigned long long t0 = gtimer();
           int ok = 1;
-          while (ld_acquire_i(&A.progress[s - 1]) < need) {
-            if (gtimer() - t0 > GBHE_WAIT_NS || ld_acquire_i(&A.st[ST_ERR]) != 0) {
+          unsigned pause = 16, polls = 0;
+          while (ld_acquire_i(&A.progress[(size_t)(s - 1) * PSTRIDE]) < need) {
+            if ((++polls & 63) == 0 && (gtimer() - t0 > GBHE_WAIT_NS || ld_acquire_i(&A.st[ST_ERR]) != 0)) {
               set_err_once(A.st, GBHE_ETIMEOUT);
               ok = 0;
               break;
             }
-            __nanosleep(32);
+            __nanosleep(pause);
+            if (pause < 256) pause <<= 1;
           }
           S.ok = ok;
         }
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
       // publish progress
       if (t == 0) {
         __threadfence();
-        st_release_i(&A.progress[s], j + 1);
+        st_release_i(&A.progress[(size_t)s * PSTRIDE], j + 1);
       }
     }
   }
@@ -288,7 +293,7 @@ __global__ void k_band_out(const cplx* WB, int ldb, int n, double* d, double* e)
 }  // namespace
 
 size_t hb2st_ws_bytes(int n, int nb) {
-  return (size_t)(2 * nb + 1) * std::max(n, 1) * sizeof(cplx) + (size_t)std::max(n, 1) * sizeof(int) + 512;
+  return (size_t)(2 * nb + 1) * std::max(n, 1) * sizeof(cplx) + (size_t)std::max(n, 1) * PSTRIDE * sizeof(int) + 512;
 }
 
 int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* e, cplx* V2, cplx* tau2) {
@@ -298,13 +303,13 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
   const size_t save = a.off;
   const int ldb = 2 * nb + 1;
   cplx* WB = a.take<cplx>((size_t)ldb * n);
-  int* prog = a.take<int>(n);
+  int* prog = a.take<int>((size_t)n * PSTRIDE);
   if (!a.ok() || !WB) { a.off = save; return GBHE_EWORKSPACE; }
   const int J = hb2st_J(n, nb);
   k_band_in<<<std::min<size_t>(((size_t)ldb * n + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, n, nb, WB, ldb);
   count_launch();
   GBHE_CUDA(cudaGetLastError());
-  GBHE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * n, c.st));
+  GBHE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)n * PSTRIDE, c.st));
   if (n >= 2) {
     ChaseArgs ca;
     ca.WB = WB; ca.ldb = ldb; ca.n = n; ca.nb = nb; ca.J = J; ca.V2 = V2; ca.tau2 = tau2;
