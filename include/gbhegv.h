@@ -159,6 +159,26 @@ int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B,
 int gbhe_hegv_onestage(gbhe_handle h, int n, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il,
                        int iu, double* w, gbhe_cplx* X, int ldx, void* stream);
 
+/* Many independent problems of uneven sizes (the repeated solves that
+ * motivate the paper, Section 1): problem i is gbhe_hegv(n[i], nb[i], A[i],
+ * lda[i], B[i], ldb[i], il[i], iu[i], w[i], X[i], ldx[i]) on worker stream
+ * workers[k] with handle hs[k], k = assign[i] from gbhe_batched_plan (largest
+ * problems first, each to the worker with the least n^3 work so far;
+ * deterministic).  Each hs[k] needs the workspace of the largest problem it
+ * is assigned (gbhe_workspace_size with that n, nb and m = iu - il + 1).  The
+ * workers are forked from `stream` (they wait for the work already on it) and
+ * joined back with the handles' events, so the batch is ordered on `stream`:
+ * capturing `stream` into a CUDA graph captures every solve, and later
+ * launches of that graph repeat them.  Before the first capture, solve once
+ * outside capture (first use sets up device constants), and pass no status
+ * checks during capture (gbhe_get_status synchronises).  Returns 0, a negative
+ * argument index (-5: an argument of some problem) or a GBHE_E* code; the
+ * join is enqueued in every case.  The paper has no counterpart. */
+int gbhe_batched_plan(int nworkers, int count, const int* n, int* assign);
+int gbhe_hegv_batched(gbhe_handle* hs, void* const* workers, int nworkers, int count, const int* n, const int* nb,
+                      gbhe_cplx* const* A, const int* lda, gbhe_cplx* const* B, const int* ldb, const int* il,
+                      const int* iu, double* const* w, gbhe_cplx* const* X, const int* ldx, void* stream);
+
 /* The FP64 tensor-core (DMMA) GEMM that every level-3 step above uses,
  * exposed for testing and profiling:  C = alpha op(A) op(B) + beta C, complex128
  * column-major.  opA in {0: N, 1: T, 2: C (conjugate transpose), 3: Hermitian

@@ -129,6 +129,10 @@ int gbhe_create(gbhe_handle* handle, int device) {
   h->spin_limit = 0;
   h->engine = GBHE_ENGINE_CRT;
   h->crt_block = CRT_BLOCK;
+  if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(h->status); cudaFreeHost(h->status_host); delete h; return GBHE_ECUDA;
+  }
   *handle = h;
   return 0;
 }
@@ -136,6 +140,8 @@ int gbhe_create(gbhe_handle* handle, int device) {
 int gbhe_destroy(gbhe_handle h) {
   if (!h) return 0;
   cudaSetDevice(h->device);
+  cudaEventDestroy(h->ev_fork);
+  cudaEventDestroy(h->ev_join);
   cudaFree(h->status);
   cudaFreeHost(h->status_host);
   delete h;

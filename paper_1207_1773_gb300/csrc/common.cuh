@@ -145,6 +145,8 @@ struct gbhe_ctx {
   unsigned spin_limit;  // test hook (0 = default)
   int engine;           // GBHE_ENGINE_CRT (default) or GBHE_ENGINE_DMMA
   int crt_block;        // largest tensor-core GEMM block (workspace vs speed)
+  cudaEvent_t ev_fork;  // fork / join events of gbhe_hegv_batched
+  cudaEvent_t ev_join;
 };
 
 #define GBHE_CUDA(call)                                      \

@@ -181,47 +181,57 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
   __syncthreads();
   const int ncomp = o.cplx ? 2 : 1;
   const size_t plane = (size_t)o.R * Kp;
-  for (int q = ty; q < 32; q += 8) {
-    const int r = r0 + q, k = k0 + tx;  // k contiguous in the output
-    if (r >= o.R || k >= Kp) continue;
-    const double2 v = tile[q][tx];
-    const int er = e[r];
-    // scaled integers (|v| <= 2^52) as sign + three 18-bit limbs
-    bool sg[2];
-    unsigned a[2], b[2], c[2];
+  // each thread: one row, four consecutive k (one 8-byte store per plane)
+  const int t = ty * 32 + tx, q = t >> 3, kq = (t & 7) * 4;
+  const int r = r0 + q, k = k0 + kq;
+  if (r >= o.R) return;
+  const int er = e[r];
+  // scaled integers (|v| <= 2^52) as sign + three 18-bit limbs
+  bool sg[4][2];
+  unsigned a[4][2], b[4][2], c[4][2];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double2 v = tile[q][kq + u];
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
       const double x = part ? v.y : v.x;
       const long long bits = __double_as_longlong(x);
       const int E = (int)((bits >> 52) & 0x7FF);
       unsigned long long mag = 0;
-      if (E != 0 && k < o.K) {
+      if (E != 0 && k + u < o.K) {
         const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
         const int sh = er - (E - 1023);  // right shift (>= 1)
         if (sh <= 60) mag = (mant + (1ull << (sh - 1))) >> sh;
       }
-      sg[part] = bits < 0;
-      a[part] = (unsigned)(mag >> 36);
-      b[part] = (unsigned)((mag >> 18) & 0x3FFFF);
-      c[part] = (unsigned)(mag & 0x3FFFF);
+      sg[u][part] = bits < 0;
+      a[u][part] = (unsigned)(mag >> 36);
+      b[u][part] = (unsigned)((mag >> 18) & 0x3FFFF);
+      c[u][part] = (unsigned)(mag & 0x3FFFF);
     }
+  }
 #pragma unroll
-    for (int l = 0; l < NMOD; ++l) {
-      const unsigned p = (unsigned)c_p[l], bm = c_bm[l], k18 = c_k18[l], k36 = c_k36[l];
-      __half hv[2];
+  for (int l = 0; l < NMOD; ++l) {
+    const unsigned p = (unsigned)c_p[l], bm = c_bm[l], k18 = c_k18[l], k36 = c_k36[l];
 #pragma unroll
-      for (int part = 0; part < 2; ++part) {
+    for (int part = 0; part < 2; ++part) {
+      if (part == 1 && !o.cplx) break;
+      __half hv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
         // t = mag mod-equivalent below 2^27; Barrett: t - p floor(t bm / 2^32) lies in [0, 2p)
-        const unsigned t = a[part] * k36 + b[part] * k18 + c[part];
-        unsigned rr = t - __umulhi(t, bm) * p;
+        const unsigned tt = a[u][part] * k36 + b[u][part] * k18 + c[u][part];
+        unsigned rr = tt - __umulhi(tt, bm) * p;
         if (rr >= p) rr -= p;
         int sv = rr > (p >> 1) ? (int)rr - (int)p : (int)rr;  // symmetric, |sv| <= 128
-        if (sg[part]) sv = -sv;
-        hv[part] = __int2half_rn(sv);
+        if (sg[u][part]) sv = -sv;
+        hv[u] = __int2half_rn(sv);
       }
-      __half* dst = P + (size_t)(l * ncomp) * plane + (size_t)r * Kp + k;
-      dst[0] = hv[0];
-      if (o.cplx) dst[plane] = hv[1];
+      // Kp is a multiple of 32 and k of 4: the 8-byte store is aligned and in the row
+      __half* dst = P + (size_t)(l * ncomp + part) * plane + (size_t)r * Kp + k;
+      uint2 pk;
+      pk.x = (unsigned)__half_as_ushort(hv[0]) | ((unsigned)__half_as_ushort(hv[1]) << 16);
+      pk.y = (unsigned)__half_as_ushort(hv[2]) | ((unsigned)__half_as_ushort(hv[3]) << 16);
+      *reinterpret_cast<uint2*>(dst) = pk;
     }
   }
 }

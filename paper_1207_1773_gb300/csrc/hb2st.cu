@@ -314,7 +314,10 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     ChaseArgs ca;
     ca.WB = WB; ca.ldb = ldb; ca.n = n; ca.nb = nb; ca.J = J; ca.V2 = V2; ca.tau2 = tau2;
     ca.progress = prog; ca.st = c.status;
-    const int G = std::min(c.num_sms, n - 1);
+    // sweep s starts about 2 steps after sweep s-1 and lasts at most J steps, so
+    // at most ceil(J/2) + 1 sweeps are ever active: more CTAs would only wait
+    // (and would keep other streams' kernels off their SMs)
+    const int G = std::min(std::min(c.num_sms, n - 1), (J + 1) / 2 + 2);
     GBHE_CUDA(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChaseSmem)));
     void* args[] = {&ca};
     count_launch();

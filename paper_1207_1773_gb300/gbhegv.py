@@ -77,6 +77,8 @@ def _load():
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
             "gbhe_probe_fp64_peaks": ([I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
             "gbhe_zgemm_static": ([I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
+            "gbhe_batched_plan": ([I, I, P, P], I),
+            "gbhe_hegv_batched": ([P, P, I, I, P, P, P, P, P, P, P, P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -97,7 +99,8 @@ def exported_symbols():
                         "gbhe_trsm_lh", "gbhe_hegv", "gbhe_hegv_onestage", "gbhe_status_string",
                         "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
-                        "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block")]
+                        "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block",
+                        "gbhe_batched_plan", "gbhe_hegv_batched")]
 
 
 def status_string(code: int) -> str:
@@ -383,6 +386,59 @@ def gemm_crt(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
                                                   _ptr(A), _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C),
                                                   _ld(C), int(bool(lower)), _stream(C.device)))
     return C
+
+
+def _int_array(vals):
+    return (ctypes.c_int * max(len(vals), 1))(*[int(v) for v in vals])
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * max(len(ts), 1))(*[t.data_ptr() for t in ts])
+
+
+def batched_plan(ns, nworkers):
+    """Worker index of every problem (largest first, least n^3 work so far)."""
+    out = (ctypes.c_int * max(len(ns), 1))()
+    _check("gbhe_batched_plan", _load().gbhe_batched_plan(int(nworkers), len(ns), _int_array(ns), out))
+    return [out[i] for i in range(len(ns))]
+
+
+class BatchPool:
+    """Worker streams, one handle each, and their workspaces for
+    hegv_batched; sized by prepare() for a set of problem shapes."""
+
+    def __init__(self, nworkers=4, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        self.handles = [Handle(dev) for _ in range(nworkers)]
+        self.streams = [torch.cuda.Stream(dev) for _ in range(nworkers)]
+
+    def prepare(self, ns, nbs, ms):
+        assign = batched_plan(ns, len(self.handles))
+        for k, h in enumerate(self.handles):
+            need = 0
+            for i, a in enumerate(assign):
+                if a == k:
+                    need = max(need, h.workspace_size(ns[i], nbs[i], ms[i]))
+            if need:
+                h.ensure_bytes(need)
+        return assign
+
+
+def hegv_batched(pool, As, Bs, ils, ius, nbs, ws, Xs):
+    """Solve every A_i x = lambda B_i x for eigenpairs il_i..iu_i on the pool's
+    worker streams, ordered on the current stream (capturable).  A_i, B_i
+    (overwritten), the eigenvalue vectors ws[i] and the eigenvector blocks
+    Xs[i] (n_i x m_i, column-major) are caller-owned CUDA tensors."""
+    cnt = len(As)
+    ns = [a.shape[0] for a in As]
+    hs = (ctypes.c_void_p * len(pool.handles))(*[h.h.value for h in pool.handles])
+    strm = (ctypes.c_void_p * len(pool.streams))(*[s.cuda_stream for s in pool.streams])
+    _check("gbhe_hegv_batched", _load().gbhe_hegv_batched(
+        hs, strm, len(pool.handles), cnt, _int_array(ns), _int_array(nbs), _ptr_array(As),
+        _int_array([_ld(a) for a in As]), _ptr_array(Bs), _int_array([_ld(b) for b in Bs]), _int_array(ils),
+        _int_array(ius), _ptr_array(ws), _ptr_array(Xs), _int_array([max(_ld(x), a.shape[0]) for x, a in zip(Xs, As)]),
+        _stream(pool.device)))
 
 
 def hegv(A, B, il=1, iu=None, nb=0, onestage=False, check=True):

@@ -112,3 +112,37 @@ def test_crt_lower_only(G):
     scale = np.abs(A) @ np.abs(A).T + np.abs(C)
     assert np.all(np.abs(out - ref)[low] <= 8 * (k + 2) * EPS * scale[low])
     assert np.array_equal(out[~low], C[~low])
+
+
+def test_crt_exact_at_max_k(G):
+    """K = 65536, the largest contraction of the exactness margin (|C| <= K 2^106 < M/8):
+    integer operands, exact big-integer product rounded once."""
+    rng = np.random.default_rng(4)
+    m, n, k = 16, 8, 65536
+    A = rng.integers(-2 ** 10, 2 ** 10, (m, k)).astype(np.float64)
+    B = rng.integers(-2 ** 10, 2 ** 10, (k, n)).astype(np.float64)
+    Cd = torch.zeros((n, m), dtype=torch.float64, device=DEV).t()
+    G.gemm_crt("N", "N", G.colmajor(A, DEV, torch.float64), G.colmajor(B, DEV, torch.float64), Cd, 1.0, 0.0)
+    ref = (A.astype(object) @ B.astype(object)).astype(np.float64)
+    assert np.array_equal(Cd.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("k,cplx", [(256, True), (257, True), (512, False), (513, False)])
+def test_crt_chunk_boundaries(G, k, cplx):
+    """Either side of one exact chunk (256 complex / 512 real contraction terms):
+    the single-chunk (warp-specialised) and the multi-chunk product kernels."""
+    rng = np.random.default_rng(k)
+    m, n = 130, 70
+    if cplx:
+        A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+        B = rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+        Ad, Bd = _c(A), _c(B)
+        Cd = torch.zeros((n, m), dtype=torch.complex128, device=DEV).t()
+    else:
+        A = rng.standard_normal((m, k))
+        B = rng.standard_normal((k, n))
+        Ad, Bd = G.colmajor(A, DEV, torch.float64), G.colmajor(B, DEV, torch.float64)
+        Cd = torch.zeros((n, m), dtype=torch.float64, device=DEV).t()
+    G.gemm_crt("N", "N", Ad, Bd, Cd, 1.0, 0.0)
+    ref = A @ B
+    assert np.all(np.abs(Cd.cpu().numpy() - ref) <= 8 * (k + 2) * EPS * (np.abs(A) @ np.abs(B)))
