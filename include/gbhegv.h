@@ -179,6 +179,21 @@ int gbhe_hegv_batched(gbhe_handle* hs, void* const* workers, int nworkers, int c
                       gbhe_cplx* const* A, const int* lda, gbhe_cplx* const* B, const int* ldb, const int* il,
                       const int* iu, double* const* w, gbhe_cplx* const* X, const int* ldx, void* stream);
 
+/* Reverse-mode derivative of the selected eigenpairs il..iu of gbhe_hegv
+ * (first-order perturbation theory; the paper has no counterpart).  Inputs:
+ * the whole decomposition of the same pair -- w_all (n, ascending) and the
+ * B-orthonormal X_all (n x n, ldx), e.g. gbhe_hegv with il = 1, iu = n -- and
+ * the cotangents of the selected pairs: gw (m = iu-il+1 real) and gX (n x m,
+ * ldg), meaning dL = sum_i gw_i dlambda_i + Re sum_i gX_i^H dx_i.  Outputs
+ * (n x n, full storage, Hermitian): dA and dB with
+ * dL = Re tr(dA^H dA') + Re tr(dB^H dB') for Hermitian perturbations dA', dB'.
+ * Terms 1/(lambda_i - lambda_j) with |lambda_i - lambda_j| < delta are dropped
+ * (degenerate-gap masking; the eigenvector phase is free, so a loss must not
+ * depend on it).  Four n x n x m products on the library's GEMM engine. */
+int gbhe_hegv_adjoint(gbhe_handle h, int n, int il, int iu, const double* w_all, const gbhe_cplx* X_all, int ldx,
+                      const double* gw, const gbhe_cplx* gX, int ldg, double delta, gbhe_cplx* dA, int ldda,
+                      gbhe_cplx* dB, int lddb, void* stream);
+
 /* The FP64 tensor-core (DMMA) GEMM that every level-3 step above uses,
  * exposed for testing and profiling:  C = alpha op(A) op(B) + beta C, complex128
  * column-major.  opA in {0: N, 1: T, 2: C (conjugate transpose), 3: Hermitian

@@ -33,6 +33,7 @@ size_t stage_bytes(gbhe_handle h, int n, int nb, int m) {
   s = std::max(s, stedc_ws_bytes(n));
   s = std::max(s, unmtr_ws_bytes(n, nb, m));
   s = std::max(s, onestage_ws_bytes(n, m));
+  s = std::max(s, adjoint_ws_bytes(n, m));
   return s;
 }
 
@@ -98,6 +99,31 @@ int gbhe_set_gemm_engine(gbhe_handle h, int engine) {
   if (engine != GBHE_ENGINE_DMMA && engine != GBHE_ENGINE_CRT) return -2;
   h->engine = engine;
   return 0;
+}
+
+int gbhe_hegv_adjoint(gbhe_handle h, int n, int il, int iu, const double* w_all, const gbhe_cplx* X_all, int ldx,
+                      const double* gw, const gbhe_cplx* gX, int ldg, double delta, gbhe_cplx* dA, int ldda,
+                      gbhe_cplx* dB, int lddb, void* stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (n > 0 && (il < 1 || il > n)) return -3;
+  if (n > 0 && (iu < il || iu > n)) return -4;
+  if (n > 0 && !w_all) return -5;
+  if (n > 0 && !X_all) return -6;
+  if (ldx < std::max(1, n)) return -7;
+  if (n > 0 && !gw) return -8;
+  if (n > 0 && !gX) return -9;
+  if (ldg < std::max(1, n)) return -10;
+  if (!(delta >= 0.0)) return -11;
+  if (n > 0 && !dA) return -12;
+  if (ldda < std::max(1, n)) return -13;
+  if (n > 0 && !dB) return -14;
+  if (lddb < std::max(1, n)) return -15;
+  if (n == 0) return 0;
+  Ctx c;
+  int rc = make_ctx(h, n, stream, &c);
+  if (rc) return rc;
+  return adjoint_run(c, n, il, iu, w_all, Z_(X_all), ldx, gw, Z_(gX), ldg, delta, Z_(dA), ldda, Z_(dB), lddb);
 }
 
 int gbhe_set_crt_block(gbhe_handle h, int block) {

@@ -95,6 +95,9 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
                const cplx* tau2, const double* Z, int ldz, cplx* X, int ldx);
 
 size_t onestage_ws_bytes(int n, int m);
+size_t adjoint_ws_bytes(int n, int m);
+int adjoint_run(Ctx& c, int n, int il, int iu, const double* w_all, const cplx* X, int ldx, const double* g,
+                const cplx* G, int ldg, double delta, cplx* dA, int ldda, cplx* dB, int lddb);
 int hegv_onestage_run(Ctx& c, int n, cplx* A, int lda, cplx* B, int ldb, int il, int iu, double* w,
                       cplx* X, int ldx);
 

@@ -80,15 +80,25 @@ __host__ __device__ inline NodeR node_range(int n, int nleaf, int lev, int i) {
 }
 
 __device__ inline int* node_cnt(const DC& a, int lo) { return a.cnt + 8 * (lo / LS); }
+
+// A recorded error (non-finite input, a leaf that did not converge) stops the
+// divide and conquer: later kernels return at once, so that no index derived
+// from NaN data is ever used.
+__device__ __forceinline__ bool dc_failed(const DC& a) { return *(volatile int*)&a.st[ST_ERR] != 0; }
 enum { C_K = 0, C_ND = 1, C_ROT = 2, C_K1 = 3, C_K2 = 4, C_K3 = 5 };
 
 // ---------------------------------------------------------------- scaling
 __global__ void k_scale_tear(DC a, const double* d, const double* e) {
   __shared__ double red[1024];
+  __shared__ int bad;
   const int t = threadIdx.x, n = a.n;
+  if (t == 0) bad = 0;
+  __syncthreads();
   double m = 0.0;
-  for (int i = t; i < n; i += blockDim.x) m = fmax(m, fabs(d[i]));
-  for (int i = t; i + 1 < n; i += blockDim.x) m = fmax(m, fabs(e[i]));
+  bool nf = false;  // fmax drops NaN, so non-finite entries are flagged separately
+  for (int i = t; i < n; i += blockDim.x) { m = fmax(m, fabs(d[i])); nf |= !isfinite(d[i]); }
+  for (int i = t; i + 1 < n; i += blockDim.x) { m = fmax(m, fabs(e[i])); nf |= !isfinite(e[i]); }
+  if (nf) atomicOr(&bad, 1);
   red[t] = m;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -96,6 +106,7 @@ __global__ void k_scale_tear(DC a, const double* d, const double* e) {
     __syncthreads();
   }
   double sc = red[0];
+  if (t == 0 && bad) set_err_once(a.st, GBHE_ENONFINITE);  // NaN or Inf in (d, e)
   if (!(sc > 0.0) || !isfinite(sc)) sc = 1.0;
   if (t == 0) a.scale[0] = sc;
   const double inv = 1.0 / sc;
@@ -114,6 +125,7 @@ __global__ void k_scale_tear(DC a, const double* d, const double* e) {
 // ---------------------------------------------------------------- leaves
 // One warp per leaf; lane r owns row r of the leaf's eigenvector block.
 __global__ void __launch_bounds__(128) k_leaf(DC a) {
+  if (dc_failed(a)) return;
   __shared__ double Zs[4][LS][LS + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int leaf = blockIdx.x * 4 + warp;
@@ -178,6 +190,7 @@ __global__ void __launch_bounds__(128) k_leaf(DC a) {
 // ---------------------------------------------------------------- deflate
 // One CTA per merging node.
 __global__ void __launch_bounds__(256) k_deflate(DC a, int lev) {
+  if (dc_failed(a)) return;
   const NodeR nd = node_range(a.n, a.nleaf, lev, blockIdx.x);
   if (!nd.merge) return;
   const int lo = nd.lo, mid = nd.mid, hi = nd.hi, n0 = hi - lo, n1 = mid - lo;
@@ -272,12 +285,14 @@ __global__ void __launch_bounds__(256) k_deflate(DC a, int lev) {
 
 // ---------------------------------------------------------------- rotate
 __global__ void __launch_bounds__(256) k_rotate(DC a, int lev) {
+  if (dc_failed(a)) return;
   const NodeR nd = node_range(a.n, a.nleaf, lev, blockIdx.x);
   if (!nd.merge) return;
   const int lo = nd.lo, hi = nd.hi;
   const int nrot = node_cnt(a, lo)[C_ROT];
   for (int r = 0; r < nrot; ++r) {
     const int ca = a.scol[lo + a.rota[lo + r]], cb = a.scol[lo + a.rotb[lo + r]];
+    if (ca < lo || ca >= hi || cb < lo || cb >= hi) continue;  // never for finite data
     const double c = a.rotc[lo + r], s = a.rots[lo + r];
     for (int row = lo + threadIdx.x; row < hi; row += blockDim.x) {
       double* pa = a.Z + (size_t)row + (size_t)ca * a.n;
@@ -304,6 +319,7 @@ __device__ inline int gemm_pos(const int* cn, int type, int grp) {
 // One CTA per (node-local) column slot: slot j < k -> non-deflated column in
 // GEMM order; slot k + r -> deflated column r.
 __global__ void __launch_bounds__(128) k_gather(DC a, int lev) {
+  if (dc_failed(a)) return;
   NodeR nd;
   node_of(a, lev, blockIdx.x, nd);
   if (!nd.merge) return;
@@ -319,6 +335,7 @@ __global__ void __launch_bounds__(128) k_gather(DC a, int lev) {
     src = a.scol[lo + a.dfq[lo + (j - k)]];
     dst = lo + j;
   }
+  if (src < lo || src >= nd.hi || dst < lo || dst >= nd.hi) return;  // never for finite data
   const double* s = a.Z + (size_t)src * a.n;
   double* d = a.Zt + (size_t)dst * a.n;
   for (int row = lo + threadIdx.x; row < nd.hi; row += blockDim.x) d[row] = s[row];
@@ -345,6 +362,7 @@ __device__ void secular_eval(const double* D, const double* z, int k, int org, d
 // One thread per root.  Root i lies in (D_i, D_{i+1}) (i < k-1) or
 // (D_{k-1}, D_{k-1} + rho |z|^2] (i = k-1).
 __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
+  if (dc_failed(a)) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n) return;
   NodeR nd;
@@ -428,6 +446,7 @@ __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
 
 // ---------------------------------------------------------------- zhat
 __global__ void __launch_bounds__(128) k_zhat(DC a, int lev) {
+  if (dc_failed(a)) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n) return;
   NodeR nd;
@@ -454,6 +473,7 @@ __global__ void __launch_bounds__(128) k_zhat(DC a, int lev) {
 // ---------------------------------------------------------------- qbuild
 // One warp per root column i: Q(gemm_pos(j), i) = zhat_j/(d_j - lambda_i), normalised.
 __global__ void __launch_bounds__(128) k_qbuild(DC a, int lev) {
+  if (dc_failed(a)) return;
   const int g = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (g >= a.n) return;
   NodeR nd;
@@ -484,6 +504,7 @@ __global__ void __launch_bounds__(128) k_qbuild(DC a, int lev) {
 // new eigenvalues of the node.  One CTA per node.
 __global__ void __launch_bounds__(256) k_positions(DC a, int lev, int last, int il, int iu,
                                                    double* w_out) {
+  if (dc_failed(a)) return;
   const NodeR nd = node_range(a.n, a.nleaf, lev, blockIdx.x);
   if (!nd.merge) return;
   const int lo = nd.lo;
@@ -541,7 +562,7 @@ __global__ void k_descs(DC a, int lev, int nnodes, int last, int il, int iu, dou
   DGroupDesc* d1 = d0 + 1;
   d0->m = d1->m = 0; d0->n = d1->n = 0; d0->k = d1->k = 0;
   d0->cmap = d1->cmap = nullptr;
-  if (!nd.merge) return;
+  if (!nd.merge || dc_failed(a)) return;
   const int lo = nd.lo, mid = nd.mid, hi = nd.hi, n = a.n;
   const int* cn = node_cnt(a, lo);
   const int k = cn[C_K], k1 = cn[C_K1], k2 = cn[C_K2];
@@ -590,6 +611,7 @@ __global__ void k_crt_descs(const DGroupDesc* in, CrtDesc* out, int cnt) {
 // Copy the deflated columns to their final positions.
 __global__ void __launch_bounds__(128) k_copy_defl(DC a, int lev, int last, int il, int iu, double* Zout,
                                                    int ldz) {
+  if (dc_failed(a)) return;
   NodeR nd;
   node_of(a, lev, blockIdx.x, nd);
   if (!nd.merge) return;
@@ -611,6 +633,7 @@ __global__ void __launch_bounds__(128) k_copy_defl(DC a, int lev, int last, int 
 
 // Single-leaf problem (n <= LS): copy the selected columns out.
 __global__ void k_single_out(DC a, int il, int iu, double* w, double* Zout, int ldz) {
+  if (dc_failed(a)) return;
   const int m = iu - il + 1;
   for (int i = threadIdx.x; i < m * a.n; i += blockDim.x) {
     const int r = i % a.n, c = i / a.n;

@@ -78,6 +78,7 @@ def _load():
             "gbhe_probe_fp64_peaks": ([I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I),
             "gbhe_zgemm_static": ([I, I, I, I, I, _Cplx, P, I, P, I, _Cplx, P, I, I, P], I),
             "gbhe_batched_plan": ([I, I, P, P], I),
+            "gbhe_hegv_adjoint": ([P, I, I, I, P, P, I, P, P, I, ctypes.c_double, P, I, P, I, P], I),
             "gbhe_hegv_batched": ([P, P, I, I, P, P, P, P, P, P, P, P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -100,7 +101,7 @@ def exported_symbols():
                         "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
                         "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block",
-                        "gbhe_batched_plan", "gbhe_hegv_batched")]
+                        "gbhe_batched_plan", "gbhe_hegv_batched", "gbhe_hegv_adjoint")]
 
 
 def status_string(code: int) -> str:
@@ -386,6 +387,23 @@ def gemm_crt(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
                                                   _ptr(A), _ld(A), _ptr(B), _ld(B), _Cplx(b.real, b.imag), _ptr(C),
                                                   _ld(C), int(bool(lower)), _stream(C.device)))
     return C
+
+
+def hegv_adjoint(w_all, X_all, il, iu, gw, gX, delta):
+    """dL/dA and dL/dB (n x n Hermitian, column-major) of the eigenpairs
+    il..iu from the whole decomposition (w_all, X_all) and the cotangents
+    gw (m) and gX (n x m); see gbhe_hegv_adjoint."""
+    n = X_all.shape[0]
+    m = iu - il + 1
+    h = handle(X_all.device)
+    h.ensure_workspace(n, 0, m)
+    dA = torch.empty((n, n), dtype=torch.complex128, device=X_all.device).t()
+    dB = torch.empty((n, n), dtype=torch.complex128, device=X_all.device).t()
+    gw = gw.contiguous()
+    _check("gbhe_hegv_adjoint", _load().gbhe_hegv_adjoint(h.h, n, il, iu, _ptr(w_all), _ptr(X_all), _ld(X_all),
+                                                          _ptr(gw), _ptr(gX), _ld(gX), float(delta), _ptr(dA),
+                                                          _ld(dA), _ptr(dB), _ld(dB), _stream(X_all.device)))
+    return dA, dB
 
 
 def _int_array(vals):

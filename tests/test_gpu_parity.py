@@ -321,3 +321,34 @@ def test_hegv_clustered_illconditioned(G):
     res = np.linalg.norm(A @ X - (B @ X) * w[None, :]) / (n * EPS * np.linalg.norm(A) * np.linalg.norm(X))
     assert res <= 100
     _cluster_subspace_check(A, B, w, X, wo, Xo)
+
+
+def test_hegv_not_pd_reports_and_recovers(G):
+    """B not positive definite: the solve reports it through the status word
+    (non-PD minor or non-finite tridiagonal) and the device stays usable."""
+    n = 200
+    A, B, _ = inputs.make_pair(n, 3)
+    B[70, 70] = -5.0
+    with pytest.raises(G.GbheError) as e:
+        G.hegv(_c(A), _c(B), 1, n, nb=32)
+    assert e.value.code > 0 or e.value.code == -104
+    A, B, lam = inputs.make_pair(n, 4)
+    w, _ = G.hegv(_c(A), _c(B), 1, n, nb=32)
+    tol = 10 * n * EPS * np.linalg.norm(A, 2) / np.linalg.eigvalsh(B).min()
+    assert np.max(np.abs(_np(w) - lam)) <= tol
+
+
+def test_stedc_nonfinite_input(G):
+    """A NaN in the tridiagonal: GBHE_ENONFINITE, no eigenvector work."""
+    n = 300
+    rng = np.random.default_rng(9)
+    d = rng.standard_normal(n)
+    e = rng.standard_normal(n - 1)
+    d[17] = np.nan
+    with pytest.raises(G.GbheError) as ex:
+        G.stedc(torch.from_numpy(d).to(DEV), torch.from_numpy(e).to(DEV))
+    assert ex.value.code == -104
+    d[17] = 0.5
+    w, _ = G.stedc(torch.from_numpy(d).to(DEV), torch.from_numpy(e).to(DEV))
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    assert np.max(np.abs(_np(w) - np.linalg.eigvalsh(T))) <= 100 * n * EPS * np.abs(T).max()
