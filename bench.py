@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--batched", action="store_true",
                    help="batched workload: 64 pairs, n ~ U[500,3000] (seed 3), lowest 25%% each, one CUDA graph")
     p.add_argument("--workers", type=int, default=8, help="worker streams of the batched workload")
+    p.add_argument("--q2-case", default=None,
+                   help="profiling aid: if the file is missing, run the stages up to the back-transform on the "
+                        "--n pair and save their outputs there; if present, run only the back-transform")
     p.add_argument("--adjoint", action="store_true",
                    help="adjoint workload: n=2048 pair, lowest 64 eigenpairs, forward + backward vs forward alone")
     p.add_argument("--cache", default=None, help="directory to keep the generated input pair between runs")
@@ -576,10 +579,46 @@ def run_adjoint(args):
     return 0
 
 
+def run_q2_case(args):
+    """Profiling aid for the back-transform alone (its Q2 wavefront starts the
+    process's CRT launches): first call saves the inputs, second call runs it."""
+    import numpy as np
+    import torch
+
+    from paper_1207_1773_gb300 import gbhegv as G
+    from paper_1207_1773_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    path, n, nb = args.q2_case, args.n, args.nb
+    if not os.path.exists(path):
+        A_np, B_np, _ = inputs.make_pair(n, 1, "uniform", -10.0, 10.0, device=dev)
+        A, B = G.colmajor(A_np, dev), G.colmajor(B_np, dev)
+        G.potrf(B)
+        G.hegst(A, B)
+        T1, _ = G.he2hb(A, nb)
+        d, e, V2, tau2 = G.hb2st(A, nb)
+        _, Z = G.stedc(d, e)
+        np.savez(path, A=A.cpu().numpy(), T1=T1.cpu().numpy(), V2=V2.cpu().numpy(), tau2=tau2.cpu().numpy(),
+                 Z=Z.cpu().numpy())
+        print(json.dumps({"q2_case": path, "saved": True, "n": n, "nb": nb}))
+        return 0
+    z = np.load(path)
+    A, Z = G.colmajor(z["A"], dev), G.colmajor(z["Z"], dev)
+    T1, V2, tau2 = (torch.from_numpy(z[k]).to(dev) for k in ("T1", "V2", "tau2"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = G.unmtr_2stage(nb, A, T1, V2, tau2, Z)
+    torch.cuda.synchronize()
+    print(json.dumps({"q2_case": path, "backtransform_s": time.perf_counter() - t0,
+                      "checksum": float(X.abs().sum())}))
+    return 0
+
+
 def main():
     args = parse()
     if args.micro:
         return run_micro(args.micro)
+    if args.q2_case:
+        return run_q2_case(args)
     if args.batched:
         return run_batched(args)
     if args.adjoint:
