@@ -17,7 +17,10 @@
 // j+1: the sweeps are pipelined over persistent CTAs (sweep s on CTA s mod G),
 // handed over through per-sweep progress counters with bounded waits.
 #include <algorithm>
+#include <cooperative_groups.h>
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gbhe {
 namespace {
@@ -270,6 +273,244 @@ __global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
   }
 }
 
+// ---------------------------------------------------------------- cluster form
+// The same chase with one step split over a cluster of CS CTAs: CTA `rank`
+// owns rows rank*RS .. rank*RS+RS-1 of the step's blocks (D and E).  Every
+// row-local operation (E H_{j-1}, H^H E, D v, the two-sided update) runs on
+// the owning CTA; the three reductions (|x|^2, v^H E, p^H v) and the gathers
+// of x and p go through distributed shared memory, with five cluster barriers
+// per step.  This spreads a step's FP64 arithmetic over CS SMs, which is what
+// bounds the chase: its critical path is ~2n dependent steps.
+constexpr int CS = 4, CT = 128, RS = MAXNB / CS;
+static_assert(RS * CS == MAXNB && CT % 8 == 0, "row split");
+
+struct ClSmem {
+  cplx D[RS * LDS];  // my rows of the diagonal block, all columns (row-major, pitch LDS)
+  cplx E[RS * LDS];  // my rows of the sub-diagonal block
+  cplx vprev[MAXNB], v[MAXNB], w[MAXNB], z[MAXNB];
+  cplx half[2][MAXNB];
+  cplx pub_x[RS];     // published: my rows of x (the column the reflector is made from)
+  cplx pub_z[MAXNB];  // published: my rows' part of v^H E
+  cplx pub_p[RS];     // published: my rows of p = tau D v
+  double pub_nrm;     // published: my rows' part of |x(1:)|^2
+  cplx pub_pv;        // published: my rows' part of p^H v
+  double red[CT / 32];
+  cplx redc[CT / 32];
+  cplx tau, scal;
+  double beta;
+  int ok;
+};
+
+__device__ __forceinline__ cplx warp_sum8(cplx v) {  // sum over aligned groups of 8 lanes
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
+  extern __shared__ __align__(16) unsigned char cl_smem_raw[];
+  ClSmem& S = *reinterpret_cast<ClSmem*>(cl_smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n = A.n, nb = A.nb;
+  const int ncl = gridDim.x / CS, cid = blockIdx.x / CS;
+  const int R0 = rank * RS;
+  const int row8 = t >> 3, sub = t & 7;  // 8 threads per local row
+  ClSmem* peer[CS];
+#pragma unroll
+  for (int q = 0; q < CS; ++q) peer[q] = cl.map_shared_rank(&S, q);
+
+  for (int s = cid; s <= n - 2; s += ncl) {
+    const int ntask = (n - 1 - s + nb - 1) / nb;
+    const int ntask_prev = (s > 0) ? (n - 1 - (s - 1) + nb - 1) / nb : 0;
+    cplx tprev = mk(0.0, 0.0);
+    int Lprev = 0;
+    for (int j = 0; j < ntask; ++j) {
+      // ---- wait (rank 0) for sweep s-1 to finish step j+1, then release the cluster
+      if (rank == 0 && t == 0) {
+        int ok = 1;
+        if (s > 0) {
+          const int need = min(j + 2, ntask_prev);
+          const unsigned long long t0 = gtimer();
+          unsigned pause = 16, polls = 0;
+          while (ld_acquire_i(&A.progress[(size_t)(s - 1) * PSTRIDE]) < need) {
+            if ((++polls & 63) == 0 && (gtimer() - t0 > GBHE_WAIT_NS || ld_acquire_i(&A.st[ST_ERR]) != 0)) {
+              set_err_once(A.st, GBHE_ETIMEOUT);
+              ok = 0;
+              break;
+            }
+            __nanosleep(pause);
+            if (pause < 256) pause <<= 1;
+          }
+        }
+        S.ok = ok;
+      }
+      cl.sync();  // #1
+      if (!peer[0]->ok) {
+        cl.sync();  // nobody leaves while another CTA may still read its shared memory
+        return;
+      }
+      const int a0 = s + 1 + j * nb;
+      const int L = min(nb, n - a0);
+      const int c0 = a0 - nb;
+      const int R1 = min(L, R0 + RS), nloc = max(0, R1 - R0);
+      // ---- stage my rows of D (lower read, mirrored) and of E
+      for (int idx = t; idx < RS * MAXNB; idx += CT) {
+        const int r = idx % RS, c = idx / RS, i = R0 + r;  // consecutive threads: consecutive rows
+        if (r < nloc && c < L && c <= i) {
+          cplx d = __ldcg(bat(A, a0 + i, a0 + c));
+          if (c == i) d.y = 0.0;
+          S.D[r * LDS + c] = d;
+        }
+        if (j > 0 && r < nloc && c < Lprev) S.E[r * LDS + c] = __ldcg(bat(A, a0 + i, c0 + c));
+      }
+      for (int idx = t; idx < RS * MAXNB; idx += CT) {
+        const int r = idx / MAXNB, c = idx % MAXNB, i = R0 + r;  // consecutive threads: consecutive columns
+        if (r < nloc && c < L && c > i) S.D[r * LDS + c] = cconj(__ldcg(bat(A, a0 + c, a0 + i)));
+      }
+      if (j == 0)
+        for (int r = t; r < nloc; r += CT) S.E[r * LDS] = __ldcg(bat(A, a0 + R0 + r, s));  // x in column 0
+      __syncthreads();
+      // ---- E <- E H_{j-1}:  y = tau_prev E vprev;  E -= y vprev^H   (row-local)
+      if (j > 0) {  // j is uniform: every lane reaches the shuffle of warp_sum8
+        const bool mine = row8 < nloc;
+        cplx acc = mk(0.0, 0.0);
+        if (mine)
+          for (int c = sub; c < Lprev; c += 8) cfma(acc, S.E[row8 * LDS + c], S.vprev[c]);
+        const cplx y = cmul(tprev, warp_sum8(acc));
+        if (mine)
+          for (int c = sub; c < Lprev; c += 8) S.E[row8 * LDS + c] = csub(S.E[row8 * LDS + c], cmulc(y, S.vprev[c]));
+      }
+      __syncthreads();
+      // ---- publish x (my rows of column 0) and my part of |x(1:)|^2
+      double nrm = 0.0;
+      for (int r = t; r < nloc; r += CT) {
+        const cplx x = S.E[r * LDS];
+        S.pub_x[r] = x;
+        if (R0 + r >= 1) nrm += cabs2(x);
+      }
+      for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+      if (lane == 0) S.red[warp] = nrm;
+      __syncthreads();
+      if (t == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < CT / 32; ++q) sum += S.red[q];
+        S.pub_nrm = sum;
+      }
+      cl.sync();  // #2
+      // ---- reflector, identical in every CTA: gather x, then scale
+      if (t < L) S.v[t] = peer[t / RS]->pub_x[t % RS];
+      if (t == 0) {
+        double xn2 = 0.0;
+        for (int q = 0; q < CS; ++q) xn2 += peer[q]->pub_nrm;
+        const cplx al = peer[0]->pub_x[0];
+        if (xn2 == 0.0 && al.y == 0.0) {
+          S.tau = mk(0.0, 0.0); S.beta = al.x; S.scal = mk(0.0, 0.0);
+        } else {
+          const double nrmx = sqrt(al.x * al.x + al.y * al.y + xn2);
+          const double beta = (al.x >= 0.0) ? -nrmx : nrmx;
+          S.beta = beta;
+          S.tau = mk((beta - al.x) / beta, -al.y / beta);
+          S.scal = cinv(mk(al.x - beta, al.y));
+        }
+      }
+      __syncthreads();
+      const cplx tau = S.tau;
+      if (t >= 1 && t < L) S.v[t] = cmul(S.v[t], S.scal);
+      if (t == 0) S.v[0] = mk(1.0, 0.0);
+      for (int r = t; r < nloc; r += CT) S.E[r * LDS] = (R0 + r == 0) ? mk(S.beta, 0.0) : mk(0.0, 0.0);
+      __syncthreads();
+      if (j == 0) {
+        for (int r = t; r < nloc; r += CT) __stcg(bat(A, a0 + R0 + r, s), S.E[r * LDS]);
+      } else {
+        // ---- z = conj(tau) v^H E[:, 1:]: my rows' part, published, summed in rank order
+        {
+          const int c = t % MAXNB, h = t / MAXNB;
+          cplx acc = mk(0.0, 0.0);
+          if (c >= 1 && c < Lprev)
+            for (int r = h; r < nloc; r += 2) ccfma(acc, S.v[R0 + r], S.E[r * LDS + c]);
+          S.half[h][c] = acc;
+        }
+        __syncthreads();
+        if (t < MAXNB) S.pub_z[t] = cadd(S.half[0][t], S.half[1][t]);
+        cl.sync();  // #3
+        if (t >= 1 && t < Lprev) {
+          cplx zz = mk(0.0, 0.0);
+          for (int q = 0; q < CS; ++q) zz = cadd(zz, peer[q]->pub_z[t]);
+          S.z[t] = cmul(cconj(tau), zz);
+        }
+        __syncthreads();
+        // E[:, c] -= v z_c (c >= 1), then write my rows of E back
+        for (int idx = t; idx < RS * MAXNB; idx += CT) {
+          const int r = idx % RS, c = idx / RS;
+          if (r < nloc && c < Lprev) {
+            cplx e = S.E[r * LDS + c];
+            if (c >= 1) e = csub(e, cmul(S.v[R0 + r], S.z[c]));
+            __stcg(bat(A, a0 + R0 + r, c0 + c), e);
+          }
+        }
+      }
+      // ---- store the reflector (rank 0)
+      if (rank == 0) {
+        cplx* vout = A.V2 + ((size_t)s * A.J + j) * nb;
+        for (int i = t; i < nb; i += CT) vout[i] = (i < L) ? S.v[i] : mk(0.0, 0.0);
+        if (t == 0) A.tau2[(size_t)s * A.J + j] = tau;
+      }
+      // ---- two-sided update: p = tau D v (my rows), alpha = -1/2 tau p^H v, w = p + alpha v
+      {
+        const bool mine = row8 < nloc;
+        cplx acc = mk(0.0, 0.0);
+        if (mine)
+          for (int c = sub; c < L; c += 8) cfma(acc, S.D[row8 * LDS + c], S.v[c]);
+        const cplx pr = cmul(tau, warp_sum8(acc));  // every lane reaches the shuffle
+        if (mine && sub == 0) S.pub_p[row8] = pr;
+        // my part of p^H v: one contribution per row (the sub == 0 lane)
+        cplx pv = (row8 < nloc && sub == 0) ? cmulc(S.v[R0 + row8], pr) : mk(0.0, 0.0);  // v conj(p) = conj(p) v
+        pv = warp_sum(pv);
+        if (lane == 0) S.redc[warp] = pv;
+        __syncthreads();
+        if (t == 0) {
+          cplx sum = mk(0.0, 0.0);
+          for (int q = 0; q < CT / 32; ++q) sum = cadd(sum, S.redc[q]);
+          S.pub_pv = sum;
+        }
+      }
+      cl.sync();  // #4
+      if (t == 0) {
+        cplx pvt = mk(0.0, 0.0);
+        for (int q = 0; q < CS; ++q) pvt = cadd(pvt, peer[q]->pub_pv);
+        S.scal = cscal(-0.5, cmul(tau, pvt));
+      }
+      __syncthreads();
+      if (t < L) S.w[t] = cadd(peer[t / RS]->pub_p[t % RS], cmul(S.scal, S.v[t]));
+      __syncthreads();
+      // D -= v w^H + w v^H on my rows; write back the lower part
+      for (int idx = t; idx < RS * MAXNB; idx += CT) {
+        const int r = idx % RS, c = idx / RS, i = R0 + r;
+        if (r < nloc && c < L && c <= i) {
+          cplx d = csub(S.D[r * LDS + c], cadd(cmulc(S.v[i], S.w[c]), cmulc(S.w[i], S.v[c])));
+          if (c == i) d.y = 0.0;
+          __stcg(bat(A, a0 + i, a0 + c), d);
+        }
+      }
+      // keep H_j for the next step
+      for (int i = t; i < L; i += CT) S.vprev[i] = S.v[i];
+      tprev = tau;
+      Lprev = L;
+      __syncthreads();
+      cl.sync();  // #5: every CTA's writes (and reads of the published data) done
+      if (rank == 0 && t == 0) {
+        __threadfence();
+        st_release_i(&A.progress[(size_t)s * PSTRIDE], j + 1);
+      }
+    }
+  }
+}
+
 // Copy the lower band of A into the working band (2nb extra sub-diagonals zeroed).
 __global__ void k_band_in(const cplx* A, int lda, int n, int nb, cplx* WB, int ldb) {
   const size_t total = (size_t)ldb * n;
@@ -318,8 +559,6 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     // at most ceil(J/2) + 1 sweeps are ever active: more CTAs would only wait
     // (and would keep other streams' kernels off their SMs)
     const int G = std::min(std::min(c.num_sms, n - 1), (J + 1) / 2 + 2);
-    GBHE_CUDA(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChaseSmem)));
-    void* args[] = {&ca};
     count_launch();
     double fl = 0.0;
     if (prof_on()) {
@@ -335,7 +574,43 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     }
     const double by = 16.0 * ((double)n * J * nb + 2.0 * ldb * n);
     ProfScope prof(c.st, GBHE_PROF_CHASE, fl, by);
-    GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_chase, dim3(G), dim3(HT), args, sizeof(ChaseSmem), c.st));
+    // Cluster form (CS CTAs per sweep) when the device accepts a cooperative
+    // cluster launch with every cluster resident; decided once, outside stream
+    // capture, else the one-CTA form.
+    static int cl_state = 0;  // 0 unknown, 1 usable, -1 not usable
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GBHE_CUDA(cudaStreamIsCapturing(c.st, &cap));
+    bool launched = false;
+    if (cl_state == 1 || (cl_state == 0 && cap == cudaStreamCaptureStatusNone)) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(G * CS);
+      cfg.blockDim = dim3(CT);
+      cfg.dynamicSmemBytes = sizeof(ClSmem);
+      cfg.stream = c.st;
+      cudaLaunchAttribute at[2];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CS;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      at[1].id = cudaLaunchAttributeCooperative;
+      at[1].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 2;
+      int maxc = 0;
+      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)k_chase_cl, &cfg) == cudaSuccess && maxc >= G &&
+          cudaLaunchKernelEx(&cfg, k_chase_cl, ca) == cudaSuccess) {
+        launched = true;
+        cl_state = 1;
+      } else {
+        (void)cudaGetLastError();
+        if (cl_state == 0) cl_state = -1;
+      }
+    }
+    if (!launched) {
+      GBHE_CUDA(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChaseSmem)));
+      void* args[] = {&ca};
+      GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_chase, dim3(G), dim3(HT), args, sizeof(ChaseSmem), c.st));
+    }
   }
   k_band_out<<<std::min((n + 255) / 256, 1024), 256, 0, c.st>>>(WB, ldb, n, d, e);
   count_launch();
