@@ -194,12 +194,15 @@ int gbhe_hegv_adjoint(gbhe_handle h, int n, int il, int iu, const double* w_all,
                       const double* gw, const gbhe_cplx* gX, int ldg, double delta, gbhe_cplx* dA, int ldda,
                       gbhe_cplx* dB, int lddb, void* stream);
 
-/* The FP64 tensor-core (DMMA) GEMM that every level-3 step above uses,
- * exposed for testing and profiling:  C = alpha op(A) op(B) + beta C, complex128
- * column-major.  opA in {0: N, 1: T, 2: C (conjugate transpose), 3: Hermitian
- * matrix read from its lower triangle}; opB in {0: N, 1: T, 2: C}.  lower != 0
- * writes only C(i,j) with i >= j.  Not part of Algorithms 1-2; the paper has
- * no counterpart beyond "level 3 BLAS on the GPU" (Section 3). */
+/* The complex GEMM that every level-3 step above uses, through the engine
+ * selected on the handle (gbhe_set_gemm_engine: the tensor-core CRT GEMM for
+ * large products, cut into blocks of gbhe_set_crt_block, and the FP64 DMMA
+ * GEMM for small ones), exposed for testing and profiling:
+ * C = alpha op(A) op(B) + beta C, complex128 column-major.  opA in {0: N,
+ * 1: T, 2: C (conjugate transpose), 3: Hermitian matrix read from its lower
+ * triangle}; opB in {0: N, 1: T, 2: C}.  lower != 0 writes only C(i,j) with
+ * i >= j.  Not part of Algorithms 1-2; the paper has no counterpart beyond
+ * "level 3 BLAS on the GPU" (Section 3). */
 int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const gbhe_cplx* A,
                int lda, const gbhe_cplx* B, int ldb, gbhe_cplx beta, gbhe_cplx* C, int ldc, int lower,
                void* stream);

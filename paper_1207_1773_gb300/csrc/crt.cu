@@ -387,9 +387,10 @@ __device__ __forceinline__ void tmem_ld16(unsigned addr, float (&v)[16]) {
 // planes and outputs are sized for maxM / maxN, the layout inside an entry's
 // planes uses the entry's own M, N.  lower != 0 skips tiles strictly above the
 // diagonal (their outputs are never read).  Timeouts of the bounded waits
-// record GBHE_ETIMEOUT in status[ST_ERR].  ONE: every modulus is a single
-// exact chunk (Kp <= KC_TERMS), so no running residues are kept.
-template <bool CPLX, bool ONE>
+// record GBHE_ETIMEOUT in status[ST_ERR].  Used for products whose moduli span
+// several exact chunks (Kp > KC_TERMS); single-chunk products use
+// k_crt_umma_ws below.
+template <bool CPLX>
 __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, const __half* PB, int M, int N, int Kp,
                                                          unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
                                                          int lower, int mpc, int* status) {
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   };
 
   // running residues of this thread's row (32 q + lane) and 64 columns (64 h + x)
-  constexpr int NRES = ONE ? 1 : 64;
+  constexpr int NRES = 64;
   float res[NC][NRES];
 #pragma unroll
   for (int c = 0; c < NC; ++c)
@@ -494,51 +495,29 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     const float p = (float)c_p[l], pinv = c_pinv[l];
     const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(64 * h);
     const int il = 32 * q + lane;
-    if constexpr (ONE) {
-      // the modulus' only chunk: reduce straight to bytes
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        float P[NC][16];
+    for (int sl = 0; sl < 4; ++sl) {
+      float P[NC][16];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
+      for (int c = 0; c < NC; ++c)
 #pragma unroll
-          for (int x = 0; x < 16; ++x) {
-            float v = red_sym(P[c][x], p, pinv);  // |v| <= p/2 + 1
-            if (v < 0.f) v += p;                  // [0, p)
-            stile[(c * UBN + 64 * h + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
-          }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    } else {
+        for (int x = 0; x < 16; ++x) res[c][sl * 16 + x] += red_sym(P[c][x], p, pinv);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if ((u % nch) == nch - 1) {
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        float P[NC][16];
+      for (int x = 0; x < NRES; ++x) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int x = 0; x < 16; ++x) res[c][sl * 16 + x] += red_sym(P[c][x], p, pinv);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      if ((u % nch) == nch - 1) {
-#pragma unroll
-        for (int x = 0; x < NRES; ++x) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            float v = red_sym(res[c][x], p, pinv);
-            if (v < 0.f) v += p;  // [0, p)
-            stile[(c * UBN + 64 * h + x) * OPITCH + il] = (unsigned char)(int)v;
-            res[c][x] = 0.f;
-          }
+        for (int c = 0; c < NC; ++c) {
+          float v = red_sym(res[c][x], p, pinv);
+          if (v < 0.f) v += p;  // [0, p)
+          stile[(c * UBN + 64 * h + x) * OPITCH + il] = (unsigned char)(int)v;
+          res[c][x] = 0.f;
         }
       }
-    }
-    if (ONE || (u % nch) == nch - 1) {
       __syncthreads();
       // the two CBN-wide layout tiles of this CTA
       const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
@@ -1058,7 +1037,7 @@ int umma_prepare(int* nsm_out) {
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma_ws<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WsCfg<CPLX>::SMEM));
     else
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)UCfg<CPLX>::SMEM));
     int dev = 0;
     GBHE_CUDA(cudaGetDevice(&dev));
@@ -1086,7 +1065,7 @@ int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int 
     k_crt_umma_ws<CPLX><<<grid, WS_THREADS, WsCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
                                                                       mpc, status);
   else
-    k_crt_umma<CPLX, false><<<grid, UTHREADS, UCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
+    k_crt_umma<CPLX><<<grid, UTHREADS, UCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
                                                                        mpc, status);
   count_launch();
   return 0;
