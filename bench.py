@@ -15,10 +15,9 @@ N(n, m) = (32/3) n^3 + 12 n^2 m real flops (identical for one- and two-stage).
                   [--n 10000] [--frac 1.0] [--nb 64] [--no-e2e] [--no-onestage]
 
 --impl reference times the CPU oracle (plain C, FP64, one-stage) on a bounded
-sample of the same workload (n = 1536) on the host cores.
-Under torchrun (N > 1) every rank solves its own replica (the method does not
-shard across GPUs in this build: replicas only); value = all ranks' flops /
-max rank time.
+sample of the same workload (n = 2048) on the host cores.
+Under torchrun (N > 1) every rank solves its own replica (the solver runs on
+one GPU: replicas only); value = all ranks' flops / max rank time.
 """
 from __future__ import annotations
 
@@ -28,6 +27,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -138,7 +138,7 @@ class Clocks:
 
     def __init__(self, gpu_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = os.path.join(tempfile.gettempdir(), "gbhegv_clocks_bench.csv")
         self.gpu = gpu_index
 
     def start(self):
