@@ -84,6 +84,23 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(ms, dist_mod, device):
+    """The slowest rank's time (the job's time): all-reduce MAX over the process
+    group, or the value itself without one."""
+    if dist_mod is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(n, m, steps, world_size, ms_max):
+    """Whole-job throughput: the nominal flops of every rank's replicas over the
+    slowest rank's time."""
+    return nominal_flops(n, m) * steps * world_size / (ms_max * 1e-3) / 1e9
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -261,12 +278,9 @@ def run_ours(args):
     st = h.status()
     if st != 0:
         raise RuntimeError("solver status %d in the timed region" % st)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     total_flops = nominal_flops(n, m) * args.steps * ws
-    value = total_flops / (ms * 1e-3) / 1e9
+    value = job_gflops(n, m, args.steps, ws, ms)
 
     # accuracy of the last timed step against the constructed spectrum
     w_np = w.cpu().numpy()
@@ -294,12 +308,8 @@ def run_ours(args):
             wh.copy_(w2, non_blocking=True)
         f1.record(stream)
         barrier()
-        ms2 = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([ms2], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms2 = float(t.item())
-        e2e = {"value": total_flops / (ms2 * 1e-3) / 1e9, "unit": UNIT,
+        ms2 = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+        e2e = {"value": job_gflops(n, m, args.steps, ws, ms2), "unit": UNIT,
                "h2d_bytes_per_step": int(2 * n * n * 16), "d2h_bytes_per_step": int(n * m * 16 + m * 8),
                "ms_per_step": ms2 / args.steps}
 
