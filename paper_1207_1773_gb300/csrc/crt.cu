@@ -51,10 +51,12 @@ __constant__ unsigned c_M[4];            // M
 __constant__ unsigned c_k18[NMOD], c_k36[NMOD];  // 2^18 mod p, 2^36 mod p
 __constant__ unsigned c_bm[NMOD];                // floor(2^32 / p) (Barrett reduction)
 
-bool g_const_ready = false;
+bool g_const_ready[MAX_DEVICES] = {};
 
 int init_constants() {
-  if (g_const_ready) return 0;
+  const int dev = device_slot();
+  if (dev < 0) return GBHE_ECUDA;
+  if (g_const_ready[dev]) return 0;
   typedef unsigned __int128 u128;
   u128 M = 1;
   for (int l = 0; l < NMOD; ++l) M *= (u128)h_mod[l];
@@ -87,7 +89,7 @@ int init_constants() {
   GBHE_CUDA(cudaMemcpyToSymbol(c_k18, k18, sizeof(k18)));
   GBHE_CUDA(cudaMemcpyToSymbol(c_k36, k36, sizeof(k36)));
   GBHE_CUDA(cudaMemcpyToSymbol(c_bm, bm, sizeof(bm)));
-  g_const_ready = true;
+  g_const_ready[dev] = true;
   return 0;
 }
 
@@ -1030,21 +1032,21 @@ inline size_t out_bytes(int M, int N, int cplx) {
 // grid covers the GPU at least twice.
 template <bool CPLX, bool ONE>
 int umma_prepare(int* nsm_out) {
-  static bool ready = false;
-  static int nsm = 0;
-  if (!ready) {
+  static bool ready[MAX_DEVICES] = {};
+  static int nsm[MAX_DEVICES] = {};
+  const int dev = device_slot();
+  if (dev < 0) return GBHE_ECUDA;
+  if (!ready[dev]) {
     if (ONE)
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma_ws<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WsCfg<CPLX>::SMEM));
     else
       GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)UCfg<CPLX>::SMEM));
-    int dev = 0;
-    GBHE_CUDA(cudaGetDevice(&dev));
-    GBHE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    ready = true;
+    GBHE_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
+    ready[dev] = true;
   }
-  *nsm_out = nsm;
+  *nsm_out = nsm[dev];
   return 0;
 }
 

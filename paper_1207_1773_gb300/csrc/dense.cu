@@ -154,11 +154,13 @@ __global__ void k_hermitize(cplx* A, int lda, int n) {
 int diag_smem() { return 2 * DB * DB * (int)sizeof(cplx); }
 
 int ensure_attrs() {
-  static bool done = false;
-  if (done) return 0;
+  static bool done[MAX_DEVICES] = {};
+  const int dev = device_slot();
+  if (dev < 0) return GBHE_ECUDA;
+  if (done[dev]) return 0;
   GBHE_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, diag_smem()));
   GBHE_CUDA(cudaFuncSetAttribute(k_trtri_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, diag_smem()));
-  done = true;
+  done[dev] = true;
   return 0;
 }
 

@@ -308,12 +308,14 @@ __global__ void __launch_bounds__(NT, 2) k_dgemm_grouped(const DGroupDesc* desc,
 
 template <bool CPLX, int OPA, int OPB>
 int launch_mode(cudaStream_t st, dim3 grid, const GemmArgs& g, int kchunk, cplx* partial) {
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[MAX_DEVICES] = {};
+  const int dev = device_slot();
+  if (dev < 0) return GBHE_ECUDA;
+  if (!attr[dev]) {
     if (cudaFuncSetAttribute(k_gemm<CPLX, OPA, OPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<CPLX>()) != cudaSuccess)
       return GBHE_ECUDA;
-    attr = true;
+    attr[dev] = true;
   }
   k_gemm<CPLX, OPA, OPB><<<grid, NT, smem_bytes<CPLX>(), st>>>(g, kchunk, partial);
   count_launch();
@@ -392,12 +394,14 @@ int dgemm(cudaStream_t st, const GemmArgs& g, void* scratch, size_t scratch_byte
 int dgemm_grouped(cudaStream_t st, const DGroupDesc* d_desc, int ngroups, int max_m, int max_n,
                   double alpha, double beta) {
   if (ngroups <= 0 || max_m <= 0 || max_n <= 0) return 0;
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[MAX_DEVICES] = {};
+  const int dev = device_slot();
+  if (dev < 0) return GBHE_ECUDA;
+  if (!attr[dev]) {
     if (cudaFuncSetAttribute(k_dgemm_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<false>()) != cudaSuccess)
       return GBHE_ECUDA;
-    attr = true;
+    attr[dev] = true;
   }
   dim3 grid((max_m + BM - 1) / BM, (max_n + BN - 1) / BN, ngroups);
   ProfScope prof(st, GBHE_PROF_DGEMM, 0.0, 0.0);  // sizes live on the device

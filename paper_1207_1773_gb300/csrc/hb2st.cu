@@ -577,7 +577,10 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     // Cluster form (CS CTAs per sweep) when the device accepts a cooperative
     // cluster launch with every cluster resident; decided once, outside stream
     // capture, else the one-CTA form.
-    static int cl_state = 0;  // 0 unknown, 1 usable, -1 not usable
+    static int cl_states[MAX_DEVICES] = {};  // 0 unknown, 1 usable, -1 not usable
+    const int dev = device_slot();
+    if (dev < 0) { a.off = save; return GBHE_ECUDA; }
+    int& cl_state = cl_states[dev];
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     GBHE_CUDA(cudaStreamIsCapturing(c.st, &cap));
     bool launched = false;

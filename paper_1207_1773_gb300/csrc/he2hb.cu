@@ -194,10 +194,12 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
     int chunk = (mp + G - 1) / G;
     size_t smem = (size_t)chunk * nb * sizeof(cplx);
     if (smem > 200 * 1024) { a.off = save; return -3; }
-    static size_t attr_set = 0;
-    if (smem > 48 * 1024 && smem > attr_set) {
+    static size_t attr_set[MAX_DEVICES] = {};
+    const int dev = device_slot();
+    if (dev < 0) { a.off = save; return GBHE_ECUDA; }
+    if (smem > 48 * 1024 && smem > attr_set[dev]) {
       GBHE_CUDA(cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-      attr_set = 210 * 1024;
+      attr_set[dev] = 210 * 1024;
     }
     PanelArgs pa;
     pa.A = A; pa.lda = lda; pa.n = n; pa.k = k; pa.nb = nb; pa.kr = kr; pa.mp = mp; pa.chunk = chunk;

@@ -21,6 +21,17 @@ struct Ctx {
   Arena arena;                // the rest, for stage temporaries
 };
 
+// One-time set-ups (kernel attributes, __constant__ tables, launch-form
+// decisions) belong to a device, not to the process: they are kept in arrays
+// indexed by the current device.  Returns that index, or -1 when it cannot be
+// read or lies beyond MAX_DEVICES.
+constexpr int MAX_DEVICES = 64;
+inline int device_slot() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES) return -1;
+  return d;
+}
+
 constexpr size_t GEMM_SCRATCH_BYTES = size_t(32) << 20;
 // Workspace of the tensor-core FP64 GEMM: enough for one complex product of
 // min(n, block) in every dimension (about 16 GB at n = 10000 with the default
