@@ -67,6 +67,9 @@ def parse():
     p.add_argument("--n", type=int, default=10000)
     p.add_argument("--frac", type=float, default=1.0)
     p.add_argument("--nb", type=int, default=64)
+    p.add_argument("--autotune", default=None, metavar="NB,NB,...",
+                   help="time these band widths at the workload's n and fraction before the warm-up and use the "
+                        "fastest (the handle's band-width rule); overrides --nb")
     p.add_argument("--seed", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-onestage", action="store_true")
@@ -237,6 +240,11 @@ def run_ours(args):
     A = torch.empty_like(A0)
     B = torch.empty_like(B0)
     h = G.handle(dev)
+    if args.autotune:
+        from paper_1207_1773_gb300 import autotune
+        cands = tuple(int(x) for x in args.autotune.split(","))
+        autotune.autotune(h, sizes=(n,), fracs=(args.frac,), candidates=cands, seed=args.seed + rank, reps=1)
+        nb = h.resolve_nb(n, m)
     h.ensure_workspace(n, nb, m)
     dfma_peak, dmma_peak = G.probe_fp64_peaks(dev.index)
 
@@ -390,7 +398,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
             "config": {"workload": "n=%d complex128 Hermitian-definite pair, Lambda~U[-10,10], seed %d, "
                                    "lowest %d eigenpairs, nb=%d" % (n, args.seed, m, nb),
-                       "n": n, "m": m, "nb": nb, "flops_per_step": nominal_flops(n, m),
+                       "n": n, "m": m, "nb": nb,
+                       "nb_source": "autotuned over %s" % args.autotune if args.autotune else "fixed",
+                       "flops_per_step": nominal_flops(n, m),
                        "flop_convention": "(32/3)n^3 + 12 n^2 m", "l2": "inputs larger than L2 (2 x %.1f GB)"
                        % (n * n * 16 / 1e9), "parallelism": "replicas" if ws > 1 else "single GPU",
                        "workspace_gb": round(h.work_bytes / 1e9, 2)},

@@ -54,7 +54,8 @@ int gbhe_destroy(gbhe_handle handle);
 
 /* Bytes of device workspace that every entry point below needs for a
  * problem of order n, band width nb and m = iu-il+1 wanted eigenvectors
- * (an upper bound over all stages).  nb = 0 means the default band width. */
+ * (an upper bound over all stages).  nb = 0 means the band width the
+ * handle's rule gives for (n, m) (gbhe_resolve_nb). */
 int gbhe_workspace_size(gbhe_handle handle, int n, int nb, int m, size_t* bytes);
 
 /* Attach caller-owned device workspace (256-byte aligned). */
@@ -65,8 +66,35 @@ int gbhe_set_workspace(gbhe_handle handle, void* dwork, size_t bytes);
  * (potrf), or GBHE_ETIMEOUT / GBHE_ENOTCONV.  Clears the status. */
 int gbhe_get_status(gbhe_handle handle, void* stream);
 
-/* Default band width used when nb = 0 is passed. */
+/* Default band width used when nb = 0 is passed and the handle has no
+ * band-width rule (16 up to n = 128, 32 up to n = 1024, 64 beyond). */
 int gbhe_default_nb(int n);
+
+/* Band-width rule: the handle's tuning cache, filled by an autotuner that
+ * times the solve for several nb (the paper leaves nb open; it trades the
+ * stage-1 panel width against the stage-2 chase and the Q2 back-transform,
+ * both O(n^2 nb) work, Section 4.2).  `count` entries
+ * (n_max[i], frac_max[i], nb[i]); for a problem of order n with m selected
+ * pairs the rule picks the entries with the smallest n_max[i] >= n (the
+ * largest n_max when none is >= n), among those the entry with the smallest
+ * frac_max[i] >= m/n (the largest frac_max when none is; the first of equal
+ * entries), and gives its nb -- unless that nb is >= n, when the default
+ * (gbhe_default_nb) is given.  count = 0 is the default everywhere.
+ * Requirements: 0 <= count <= GBHE_NB_RULE_MAX, n_max[i] >= 1,
+ * 0 < frac_max[i] <= 1, 1 <= nb[i] <= 64; the arrays are host memory, read
+ * only during the call.  gbhe_nb_rule_pick evaluates a rule without a handle
+ * (no CUDA call) and writes the band width to *nb_out: 0, or -1 count, -2
+ * n_max, -3 frac_max, -4 nb, -5 n < 0 or m outside [0, n], -6 nb_out NULL. */
+#define GBHE_NB_RULE_MAX 64
+int gbhe_nb_rule_pick(int count, const int* n_max, const double* frac_max, const int* nb, int n, int m,
+                      int* nb_out);
+/* Install a rule on the handle (copied; replaces the previous one).  Returns
+ * 0, -1 (handle NULL) or the codes of gbhe_nb_rule_pick shifted by one
+ * (-2 count, -3 n_max, -4 frac_max, -5 nb). */
+int gbhe_set_nb_rule(gbhe_handle h, int count, const int* n_max, const double* frac_max, const int* nb);
+/* The band width that nb = 0 selects on this handle for order n and m
+ * selected pairs: 0, -1 handle NULL, -2 n < 0 or m outside [0, n], -3 nb NULL. */
+int gbhe_resolve_nb(gbhe_handle h, int n, int m, int* nb);
 
 /* Engine of the FP64 level-3 products of every stage:
  *   GBHE_ENGINE_CRT  (default) exact modular products on the FP16 tensor
@@ -149,7 +177,8 @@ int gbhe_trsm_lh(gbhe_handle h, int n, int m, const gbhe_cplx* L, int ldl, gbhe_
  * eigenpairs il..iu (1-based, inclusive) of A x = lambda B x.  A (lower
  * read) and B (lower read) are overwritten (A by band/V1 data, B by L);
  * w (m) ascending eigenvalues, X (n x m, ldx) B-orthonormal eigenvectors.
- * nb = 0 selects the default band width; 1 <= nb <= 64. */
+ * nb = 0 selects the handle's band width for (n, m = iu-il+1)
+ * (gbhe_resolve_nb); 1 <= nb <= 64. */
 int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B, int ldb, int il,
               int iu, double* w, gbhe_cplx* X, int ldx, void* stream);
 

@@ -20,6 +20,45 @@ int default_nb(int n) {
   return 64;
 }
 
+int nb_rule_check(int count, const int* n_max, const double* frac_max, const int* nb) {
+  if (count < 0 || count > GBHE_NB_RULE_MAX) return -1;
+  if (count > 0 && !n_max) return -2;
+  if (count > 0 && !frac_max) return -3;
+  if (count > 0 && !nb) return -4;
+  for (int i = 0; i < count; ++i) {
+    if (n_max[i] < 1) return -2;
+    if (!(frac_max[i] > 0.0 && frac_max[i] <= 1.0)) return -3;
+    if (nb[i] < 1 || nb[i] > 64) return -4;
+  }
+  return 0;
+}
+
+// The entries of the smallest n_max >= n (else of the largest n_max); among
+// them the smallest frac_max >= m/n (else the largest frac_max); the first of
+// equal entries.  An nb that is not below n gives way to the default.
+int nb_rule_eval(int count, const int* n_max, const double* frac_max, const int* nb, int n, int m) {
+  if (count == 0) return default_nb(n);
+  int nsel = -1, nbig = n_max[0];
+  for (int i = 0; i < count; ++i) {
+    nbig = std::max(nbig, n_max[i]);
+    if (n_max[i] >= n && (nsel < 0 || n_max[i] < nsel)) nsel = n_max[i];
+  }
+  if (nsel < 0) nsel = nbig;
+  const double f = n > 0 ? (double)m / n : 1.0;
+  int fit = -1, big = -1;
+  for (int i = 0; i < count; ++i) {
+    if (n_max[i] != nsel) continue;
+    if (big < 0 || frac_max[i] > frac_max[big]) big = i;
+    if (frac_max[i] >= f && (fit < 0 || frac_max[i] < frac_max[fit])) fit = i;
+  }
+  const int v = nb[fit >= 0 ? fit : big];
+  return v < n ? v : default_nb(n);
+}
+
+int resolve_nb(gbhe_handle h, int n, int m) {
+  return nb_rule_eval(h->nbr_count, h->nbr_n, h->nbr_f, h->nbr_nb, n, m);
+}
+
 // Workspace every call carves first: split-K scratch and the diagonal-block
 // inverses.
 size_t common_bytes(gbhe_handle h, int n) {
@@ -94,6 +133,37 @@ extern "C" {
 
 int gbhe_default_nb(int n) { return default_nb(n); }
 
+int gbhe_nb_rule_pick(int count, const int* n_max, const double* frac_max, const int* nb, int n, int m,
+                      int* nb_out) {
+  const int rc = nb_rule_check(count, n_max, frac_max, nb);
+  if (rc) return rc;
+  if (n < 0 || m < 0 || m > n) return -5;
+  if (!nb_out) return -6;
+  *nb_out = nb_rule_eval(count, n_max, frac_max, nb, n, m);
+  return 0;
+}
+
+int gbhe_set_nb_rule(gbhe_handle h, int count, const int* n_max, const double* frac_max, const int* nb) {
+  if (!h) return -1;
+  const int rc = nb_rule_check(count, n_max, frac_max, nb);
+  if (rc) return rc - 1;
+  for (int i = 0; i < count; ++i) {
+    h->nbr_n[i] = n_max[i];
+    h->nbr_f[i] = frac_max[i];
+    h->nbr_nb[i] = nb[i];
+  }
+  h->nbr_count = count;
+  return 0;
+}
+
+int gbhe_resolve_nb(gbhe_handle h, int n, int m, int* nb) {
+  if (!h) return -1;
+  if (n < 0 || m < 0 || m > n) return -2;
+  if (!nb) return -3;
+  *nb = resolve_nb(h, n, m);
+  return 0;
+}
+
 int gbhe_set_gemm_engine(gbhe_handle h, int engine) {
   if (!h) return -1;
   if (engine != GBHE_ENGINE_DMMA && engine != GBHE_ENGINE_CRT) return -2;
@@ -155,6 +225,7 @@ int gbhe_create(gbhe_handle* handle, int device) {
   h->spin_limit = 0;
   h->engine = GBHE_ENGINE_CRT;
   h->crt_block = CRT_BLOCK;
+  h->nbr_count = 0;
   if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     cudaFree(h->status); cudaFreeHost(h->status_host); delete h; return GBHE_ECUDA;
@@ -177,9 +248,9 @@ int gbhe_destroy(gbhe_handle h) {
 int gbhe_workspace_size(gbhe_handle h, int n, int nb, int m, size_t* bytes) {
   if (!h) return -1;
   if (n < 0) return -2;
-  if (nb == 0) nb = default_nb(n);
-  if (nb < 1 || nb > 128) return -3;
   if (m < 0 || m > n) return -4;
+  if (nb == 0) nb = resolve_nb(h, n, m);
+  if (nb < 1 || nb > 128) return -3;
   if (!bytes) return -5;
   *bytes = common_bytes(h, n) + driver_bytes(n, nb, m) + stage_bytes(h, n, nb, m) + 4096;
   return 0;
@@ -342,7 +413,7 @@ int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B,
               double* w, gbhe_cplx* X, int ldx, void* stream) {
   if (!h) return -1;
   if (n < 0) return -2;
-  if (nb == 0) nb = default_nb(n);
+  if (nb == 0) nb = (n > 0 && il >= 1 && iu >= il && iu <= n) ? resolve_nb(h, n, iu - il + 1) : default_nb(n);
   if (nb < 1 || nb > 64) return -3;
   if (n > 0 && !A) return -4;
   if (lda < std::max(1, n)) return -5;

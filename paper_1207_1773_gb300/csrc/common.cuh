@@ -147,6 +147,10 @@ struct gbhe_ctx {
   int crt_block;        // largest tensor-core GEMM block (workspace vs speed)
   cudaEvent_t ev_fork;  // fork / join events of gbhe_hegv_batched
   cudaEvent_t ev_join;
+  int nbr_count;        // band-width rule (gbhe_set_nb_rule); 0 = default
+  int nbr_n[GBHE_NB_RULE_MAX];
+  double nbr_f[GBHE_NB_RULE_MAX];
+  int nbr_nb[GBHE_NB_RULE_MAX];
 };
 
 #define GBHE_CUDA(call)                                      \

@@ -80,6 +80,9 @@ def _load():
             "gbhe_batched_plan": ([I, I, P, P], I),
             "gbhe_hegv_adjoint": ([P, I, I, I, P, P, I, P, P, I, ctypes.c_double, P, I, P, I, P], I),
             "gbhe_hegv_batched": ([P, P, I, I, P, P, P, P, P, P, P, P, P, P, P, P], I),
+            "gbhe_nb_rule_pick": ([I, P, P, P, I, I, ctypes.POINTER(I)], I),
+            "gbhe_set_nb_rule": ([P, I, P, P, P], I),
+            "gbhe_resolve_nb": ([P, I, I, ctypes.POINTER(I)], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -101,7 +104,8 @@ def exported_symbols():
                         "gbhe_zgemm", "gbhe_launch_count", "gbhe_profile_enable", "gbhe_profile_read",
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
                         "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block",
-                        "gbhe_batched_plan", "gbhe_hegv_batched", "gbhe_hegv_adjoint")]
+                        "gbhe_batched_plan", "gbhe_hegv_batched", "gbhe_hegv_adjoint",
+                        "gbhe_nb_rule_pick", "gbhe_set_nb_rule", "gbhe_resolve_nb")]
 
 
 def status_string(code: int) -> str:
@@ -169,6 +173,38 @@ class Handle:
 
     def status(self):
         return int(_load().gbhe_get_status(self.h, _stream(self.device)))
+
+    def set_nb_rule(self, rule):
+        """Install a band-width rule, a list of (n_max, frac_max, nb) entries
+        (empty: the default band width everywhere)."""
+        cnt, nm, fm, nbs = _rule_arrays(rule)
+        _check("gbhe_set_nb_rule", _load().gbhe_set_nb_rule(self.h, cnt, nm, fm, nbs))
+
+    def resolve_nb(self, n, m=None):
+        """The band width nb = 0 selects on this handle for order n and m pairs."""
+        m = n if m is None else m
+        out = ctypes.c_int()
+        _check("gbhe_resolve_nb", _load().gbhe_resolve_nb(self.h, int(n), int(m), ctypes.byref(out)))
+        return out.value
+
+
+def _rule_arrays(rule):
+    rule = list(rule)
+    k = max(len(rule), 1)
+    nm = (ctypes.c_int * k)(*[int(e[0]) for e in rule])
+    fm = (ctypes.c_double * k)(*[float(e[1]) for e in rule])
+    nbs = (ctypes.c_int * k)(*[int(e[2]) for e in rule])
+    return len(rule), nm, fm, nbs
+
+
+def nb_rule_pick(rule, n, m=None):
+    """Band width a rule of (n_max, frac_max, nb) entries gives for order n and
+    m selected pairs (host-only; the same lookup nb = 0 does on a handle)."""
+    m = n if m is None else m
+    cnt, nm, fm, nbs = _rule_arrays(rule)
+    out = ctypes.c_int()
+    _check("gbhe_nb_rule_pick", _load().gbhe_nb_rule_pick(cnt, nm, fm, nbs, int(n), int(m), ctypes.byref(out)))
+    return out.value
 
 
 _handles = {}
@@ -468,7 +504,7 @@ def hegv(A, B, il=1, iu=None, nb=0, onestage=False, check=True):
     n = A.shape[0]
     iu = n if iu is None else iu
     m = iu - il + 1
-    nbu = nb if nb else _load().gbhe_default_nb(n)
+    nbu = nb if nb else (h.resolve_nb(n, m) if 0 <= m <= n else _load().gbhe_default_nb(n))
     h.ensure_workspace(n, nbu, m)
     w = torch.zeros(max(m, 1), dtype=torch.float64, device=A.device)
     X = torch.zeros((max(m, 1), n), dtype=torch.complex128, device=A.device).t()
