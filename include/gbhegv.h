@@ -301,6 +301,16 @@ int gbhe_profile_read(int cls, unsigned long long* launches, double* flops, doub
 /* Human-readable text for a return/status code. */
 const char* gbhe_status_string(int code);
 
+/* Failure-detection self-test (no GPU fault): enqueues on `stream` one kernel
+ * that enters the library's bounded device wait (the grid barrier of the
+ * cooperative kernels) for a partner that never arrives.  The wait gives up
+ * after its time limit (2 s of %globaltimer), records GBHE_ETIMEOUT in the
+ * handle's status word and returns normally; the next gbhe_get_status
+ * returns GBHE_ETIMEOUT and clears the status, after which the handle and
+ * the context are usable as before.  Returns 0, -1 (handle NULL) or
+ * GBHE_ECUDA. */
+int gbhe_wait_selftest(gbhe_handle h, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

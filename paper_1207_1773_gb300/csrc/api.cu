@@ -222,7 +222,6 @@ int gbhe_create(gbhe_handle* handle, int device) {
   }
   h->work = nullptr;
   h->work_bytes = 0;
-  h->spin_limit = 0;
   h->engine = GBHE_ENGINE_CRT;
   h->crt_block = CRT_BLOCK;
   h->nbr_count = 0;

@@ -40,9 +40,9 @@ __host__ __device__ __forceinline__ cplx cinv(cplx z) {
 __host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) { return cmul(a, cinv(b)); }
 
 // Device status words (one per handle).  word[0] = info (first numerical
-// failure), word[1] = error code (GBHE_ETIMEOUT ...), words[2..] scratch for
-// barriers and counters.
-enum { ST_INFO = 0, ST_ERR = 1, ST_BAR = 4, ST_WORDS = 64 };
+// failure), word[1] = error code (GBHE_ETIMEOUT ...), words[4..5] the grid
+// barrier of the panel QR, words[8..9] the barrier of the wait self-test.
+enum { ST_INFO = 0, ST_ERR = 1, ST_BAR = 4, ST_SELF = 8, ST_WORDS = 64 };
 
 __device__ __forceinline__ void set_info_once(int* st, int info) { atomicCAS(&st[ST_INFO], 0, info); }
 __device__ __forceinline__ void set_err_once(int* st, int err) { atomicCAS(&st[ST_ERR], 0, err); }
@@ -142,7 +142,6 @@ struct gbhe_ctx {
   int* status_host;     // pinned host mirror
   void* work;           // caller-owned device workspace
   size_t work_bytes;
-  unsigned spin_limit;  // test hook (0 = default)
   int engine;           // GBHE_ENGINE_CRT (default) or GBHE_ENGINE_DMMA
   int crt_block;        // largest tensor-core GEMM block (workspace vs speed)
   cudaEvent_t ev_fork;  // fork / join events of gbhe_hegv_batched

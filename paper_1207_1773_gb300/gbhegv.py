@@ -83,6 +83,7 @@ def _load():
             "gbhe_nb_rule_pick": ([I, P, P, P, I, I, ctypes.POINTER(I)], I),
             "gbhe_set_nb_rule": ([P, I, P, P, P], I),
             "gbhe_resolve_nb": ([P, I, I, ctypes.POINTER(I)], I),
+            "gbhe_wait_selftest": ([P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -105,7 +106,7 @@ def exported_symbols():
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
                         "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block",
                         "gbhe_batched_plan", "gbhe_hegv_batched", "gbhe_hegv_adjoint",
-                        "gbhe_nb_rule_pick", "gbhe_set_nb_rule", "gbhe_resolve_nb")]
+                        "gbhe_nb_rule_pick", "gbhe_set_nb_rule", "gbhe_resolve_nb", "gbhe_wait_selftest")]
 
 
 def status_string(code: int) -> str:
@@ -333,6 +334,15 @@ def trsm_lh(L, X):
 
 PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6, "crt": 7,
                 "crt_prep": 8, "crt_mma": 9, "crt_rec": 10}
+
+
+def wait_selftest(device=None):
+    """Run the bounded-wait self-test on the handle of `device` and return the
+    status it leaves (GBHE_ETIMEOUT = -103 when the wait expired as designed;
+    the status is cleared)."""
+    h = handle(device)
+    _check("gbhe_wait_selftest", _load().gbhe_wait_selftest(h.h, _stream(h.device)))
+    return h.status()
 
 
 def launch_count() -> int:
