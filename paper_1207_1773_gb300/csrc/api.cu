@@ -441,13 +441,20 @@ int gbhe_hegv(gbhe_handle h, int n, int nb, gbhe_cplx* A, int lda, gbhe_cplx* B,
   if (!ar.ok() || !Z) return GBHE_EWORKSPACE;
   cplx* Ac = Z_(A);
   cplx* L = Z_(B);
-  if ((rc = potrf_run(c, n, L, ldb))) return rc;
-  if ((rc = hegst_run(c, n, Ac, lda, L, ldb))) return rc;
-  if ((rc = he2hb_run(c, n, nb, Ac, lda, T1, tau1))) return rc;
-  if ((rc = hb2st_run(c, n, nb, Ac, lda, d, e, V2, tau2))) return rc;
-  if ((rc = stedc_run(c, n, d, e, il, iu, w, Z, n))) return rc;
-  if ((rc = unmtr2_run(c, n, nb, m, Ac, lda, T1, V2, tau2, Z, n, Z_(X), ldx))) return rc;
-  if ((rc = trsm_run(c, 1, n, m, L, ldb, Z_(X), ldx))) return rc;
+  NvtxRange all("gbhe_hegv");
+#define GBHE_STAGE(name, call)   \
+  do {                           \
+    NvtxRange r_(name);          \
+    if ((rc = (call))) return rc; \
+  } while (0)
+  GBHE_STAGE("potrf", potrf_run(c, n, L, ldb));
+  GBHE_STAGE("hegst", hegst_run(c, n, Ac, lda, L, ldb));
+  GBHE_STAGE("he2hb", he2hb_run(c, n, nb, Ac, lda, T1, tau1));
+  GBHE_STAGE("hb2st", hb2st_run(c, n, nb, Ac, lda, d, e, V2, tau2));
+  GBHE_STAGE("stedc", stedc_run(c, n, d, e, il, iu, w, Z, n));
+  GBHE_STAGE("unmtr_2stage", unmtr2_run(c, n, nb, m, Ac, lda, T1, V2, tau2, Z, n, Z_(X), ldx));
+  GBHE_STAGE("trsm_lh", trsm_run(c, 1, n, m, L, ldb, Z_(X), ldx));
+#undef GBHE_STAGE
   return 0;
 }
 

@@ -2,8 +2,34 @@
 #pragma once
 #include "common.cuh"
 #include "gemm.cuh"
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define GBHE_HAVE_NVTX 1
+#endif
+#endif
 
 namespace gbhe {
+
+// NVTX range around a host-side stage, for Nsight timelines; a no-op when no
+// tool is attached (or when the NVTX headers are absent at build time).
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name) {
+#ifdef GBHE_HAVE_NVTX
+    nvtxRangePushA(name);
+#else
+    (void)name;
+#endif
+  }
+  ~NvtxRange() {
+#ifdef GBHE_HAVE_NVTX
+    nvtxRangePop();
+#endif
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Everything a stage needs for one call: the stream, the device status words
 // and carved pieces of the caller's workspace.
