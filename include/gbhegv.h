@@ -65,6 +65,8 @@ int gbhe_set_workspace(gbhe_handle handle, void* dwork, size_t bytes);
  * k > 0 = the leading minor of order k of B is not positive definite
  * (potrf), or GBHE_ETIMEOUT / GBHE_ENOTCONV.  Clears the status. */
 int gbhe_get_status(gbhe_handle handle, void* stream);
+/* The same call under the name of the boundary's status query. */
+int gbhe_sync_status(gbhe_handle handle, void* stream);
 
 /* Default band width used when nb = 0 is passed and the handle has no
  * band-width rule (16 up to n = 128, 32 up to n = 1024, 64 beyond). */

@@ -277,6 +277,8 @@ int gbhe_get_status(gbhe_handle h, void* stream) {
   return err;
 }
 
+int gbhe_sync_status(gbhe_handle h, void* stream) { return gbhe_get_status(h, stream); }
+
 const char* gbhe_status_string(int code) {
   switch (code) {
     case 0: return "success";

@@ -54,6 +54,7 @@ def _load():
             "gbhe_workspace_size": ([P, I, I, I, ctypes.POINTER(S)], I),
             "gbhe_set_workspace": ([P, P, S], I),
             "gbhe_get_status": ([P, P], I),
+            "gbhe_sync_status": ([P, P], I),
             "gbhe_default_nb": ([I], I),
             "gbhe_potrf": ([P, I, P, I, P], I),
             "gbhe_hegst": ([P, I, P, I, P, I, P], I),
@@ -106,7 +107,8 @@ def exported_symbols():
                         "gbhe_probe_fp64_peaks", "gbhe_crt_workspace_size", "gbhe_gemm_crt",
                         "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block",
                         "gbhe_batched_plan", "gbhe_hegv_batched", "gbhe_hegv_adjoint",
-                        "gbhe_nb_rule_pick", "gbhe_set_nb_rule", "gbhe_resolve_nb", "gbhe_wait_selftest")]
+                        "gbhe_nb_rule_pick", "gbhe_set_nb_rule", "gbhe_resolve_nb", "gbhe_wait_selftest",
+                        "gbhe_sync_status")]
 
 
 def status_string(code: int) -> str:

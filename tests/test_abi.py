@@ -61,6 +61,7 @@ def test_host_only_entry_points(lib):
     # argument checks happen before any device work
     assert lib.gbhe_potrf(None, 4, None, 4, None) == -1
     assert lib.gbhe_wait_selftest(None, None) == -1
+    assert lib.gbhe_sync_status(None, None) == -1
     assert lib.gbhe_profile_enable(0) == 0
     lib.gbhe_launch_count.restype = ctypes.c_ulonglong
     assert lib.gbhe_launch_count() == 0

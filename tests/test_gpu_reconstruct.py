@@ -48,3 +48,15 @@ def test_q1q2_reconstructs_a(G, n, nb):
     assert orth <= C, orth
     assert rec <= C, rec
     assert abs(d.sum() - np.trace(A).real) <= C * n * EPS * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("n,nb", [(1, 1), (40, 40), (40, 64)])
+def test_he2hb_band_at_least_n_is_noop(G, n, nb):
+    """With nb >= n the matrix already is a band: stage 1 leaves the lower
+    triangle as it is and stores no reflectors."""
+    A = _hermitian(n, 2000 + n)
+    Ad = G.colmajor(A, DEV)
+    T1, tau1 = G.he2hb(Ad, nb)
+    out = Ad.cpu().numpy()
+    assert np.array_equal(np.tril(out), np.tril(A))
+    assert not T1.abs().max().item() and not tau1.abs().max().item()
