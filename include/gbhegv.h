@@ -251,6 +251,14 @@ int gbhe_crt_workspace_size(int m, int n, int k, int cplx, size_t* bytes);
 int gbhe_gemm_crt(gbhe_handle h, int cplx, int opA, int opB, int m, int n, int k, gbhe_cplx alpha, const void* A,
                   int lda, const void* B, int ldb, gbhe_cplx beta, void* C, int ldc, int lower, void* stream);
 
+/* The number-theory tables of that engine, exactly as copied to the device
+ * (host-only, no CUDA call): moduli p[16]; CRT weights W[16][4], W_l =
+ * (M/p_l) * ((M/p_l)^-1 mod p_l) mod M as 128-bit little-endian 32-bit words;
+ * M[4] = prod p_l, likewise; k18[16], k36[16] = 2^18, 2^36 mod p_l (limb
+ * weights of the residue split); bm[16] = floor(2^32 / p_l) (Barrett
+ * reduction).  Any pointer may be NULL.  Returns the number of moduli. */
+int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, unsigned* k18, unsigned* k36, unsigned* bm);
+
 /* The complex DMMA GEMM of gbhe_zgemm (same operand modes and arguments, no
  * handle) for callers that cannot allocate: code that must not take device
  * memory after start-up, or that holds no handle and so has no workspace to

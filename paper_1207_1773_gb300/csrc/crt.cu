@@ -53,42 +53,53 @@ __constant__ unsigned c_bm[NMOD];                // floor(2^32 / p) (Barrett red
 
 bool g_const_ready[MAX_DEVICES] = {};
 
-int init_constants() {
-  const int dev = device_slot();
-  if (dev < 0) return GBHE_ECUDA;
-  if (g_const_ready[dev]) return 0;
+// The number-theory tables of the engine, computed on the host (the one
+// source of what init_constants copies to the device and gbhe_crt_tables
+// returns).
+struct HostTables {
+  int p[NMOD];
+  float pinv[NMOD], frac[NMOD];
+  unsigned W[NMOD][4], M[4];
+  unsigned k18[NMOD], k36[NMOD], bm[NMOD];
+};
+
+void crt_tables(HostTables& t) {
   typedef unsigned __int128 u128;
   u128 M = 1;
   for (int l = 0; l < NMOD; ++l) M *= (u128)h_mod[l];
-  int p[NMOD];
-  unsigned k18[NMOD], k36[NMOD], bm[NMOD];
-  float pinv[NMOD], frac[NMOD];
-  unsigned W[NMOD][4], Mw[4];
   for (int l = 0; l < NMOD; ++l) {
     const int pl = h_mod[l];
     const u128 Ml = M / (u128)pl;
     const int mr = (int)(Ml % (u128)pl);
     int y = 0;
-    for (int t = 1; t < pl; ++t)
-      if ((mr * t) % pl == 1) { y = t; break; }
+    for (int v = 1; v < pl; ++v)
+      if ((mr * v) % pl == 1) { y = v; break; }
     const u128 Wl = (Ml * (u128)y) % M;
-    for (int w = 0; w < 4; ++w) W[l][w] = (unsigned)(Wl >> (32 * w));
-    p[l] = pl;
-    pinv[l] = 1.0f / (float)pl;
-    frac[l] = (float)((double)y / (double)pl);
-    k18[l] = (unsigned)(((u128)1 << 18) % (u128)pl);
-    k36[l] = (unsigned)(((u128)1 << 36) % (u128)pl);
-    bm[l] = (unsigned)(((u128)1 << 32) / (u128)pl);
+    for (int w = 0; w < 4; ++w) t.W[l][w] = (unsigned)(Wl >> (32 * w));
+    t.p[l] = pl;
+    t.pinv[l] = 1.0f / (float)pl;
+    t.frac[l] = (float)((double)y / (double)pl);
+    t.k18[l] = (unsigned)(((u128)1 << 18) % (u128)pl);
+    t.k36[l] = (unsigned)(((u128)1 << 36) % (u128)pl);
+    t.bm[l] = (unsigned)(((u128)1 << 32) / (u128)pl);
   }
-  for (int w = 0; w < 4; ++w) Mw[w] = (unsigned)(M >> (32 * w));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_p, p, sizeof(p)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_pinv, pinv, sizeof(pinv)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_frac, frac, sizeof(frac)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_W, W, sizeof(W)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_M, Mw, sizeof(Mw)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_k18, k18, sizeof(k18)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_k36, k36, sizeof(k36)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_bm, bm, sizeof(bm)));
+  for (int w = 0; w < 4; ++w) t.M[w] = (unsigned)(M >> (32 * w));
+}
+
+int init_constants() {
+  const int dev = device_slot();
+  if (dev < 0) return GBHE_ECUDA;
+  if (g_const_ready[dev]) return 0;
+  HostTables t;
+  crt_tables(t);
+  GBHE_CUDA(cudaMemcpyToSymbol(c_p, t.p, sizeof(t.p)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_pinv, t.pinv, sizeof(t.pinv)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_frac, t.frac, sizeof(t.frac)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_W, t.W, sizeof(t.W)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_M, t.M, sizeof(t.M)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_k18, t.k18, sizeof(t.k18)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_k36, t.k36, sizeof(t.k36)));
+  GBHE_CUDA(cudaMemcpyToSymbol(c_bm, t.bm, sizeof(t.bm)));
   g_const_ready[dev] = true;
   return 0;
 }
@@ -1258,3 +1269,19 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
 }
 
 }  // namespace gbhe
+
+extern "C" int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, unsigned* k18, unsigned* k36, unsigned* bm) {
+  gbhe::HostTables t;
+  gbhe::crt_tables(t);
+  for (int l = 0; l < gbhe::NMOD; ++l) {
+    if (p) p[l] = t.p[l];
+    if (k18) k18[l] = t.k18[l];
+    if (k36) k36[l] = t.k36[l];
+    if (bm) bm[l] = t.bm[l];
+    for (int w = 0; w < 4; ++w)
+      if (W) W[4 * l + w] = t.W[l][w];
+  }
+  for (int w = 0; w < 4; ++w)
+    if (M) M[w] = t.M[w];
+  return gbhe::NMOD;
+}

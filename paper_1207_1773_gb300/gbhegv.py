@@ -55,6 +55,7 @@ def _load():
             "gbhe_set_workspace": ([P, P, S], I),
             "gbhe_get_status": ([P, P], I),
             "gbhe_sync_status": ([P, P], I),
+            "gbhe_crt_tables": ([P, P, P, P, P, P], I),
             "gbhe_default_nb": ([I], I),
             "gbhe_potrf": ([P, I, P, I, P], I),
             "gbhe_hegst": ([P, I, P, I, P, I, P], I),
@@ -108,7 +109,7 @@ def exported_symbols():
                         "gbhe_set_gemm_engine", "gbhe_zgemm_static", "gbhe_set_crt_block",
                         "gbhe_batched_plan", "gbhe_hegv_batched", "gbhe_hegv_adjoint",
                         "gbhe_nb_rule_pick", "gbhe_set_nb_rule", "gbhe_resolve_nb", "gbhe_wait_selftest",
-                        "gbhe_sync_status")]
+                        "gbhe_sync_status", "gbhe_crt_tables")]
 
 
 def status_string(code: int) -> str:
@@ -336,6 +337,25 @@ def trsm_lh(L, X):
 
 PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc": 5, "hemv": 6, "crt": 7,
                 "crt_prep": 8, "crt_mma": 9, "crt_rec": 10}
+
+
+def crt_tables():
+    """The tensor-core FP64 engine's tables (host-only): dict of p, W, M, k18,
+    k36, bm as Python ints (W and M joined from their 32-bit words)."""
+    k = 16
+    p = (ctypes.c_int * k)()
+    W = (ctypes.c_uint * (4 * k))()
+    M = (ctypes.c_uint * 4)()
+    k18, k36, bm = (ctypes.c_uint * k)(), (ctypes.c_uint * k)(), (ctypes.c_uint * k)()
+    nmod = _load().gbhe_crt_tables(p, W, M, k18, k36, bm)
+    if nmod != k:
+        raise RuntimeError("unexpected number of moduli %d" % nmod)
+
+    def join(words):
+        return sum(int(x) << (32 * i) for i, x in enumerate(words))
+
+    return {"p": list(p), "W": [join(W[4 * l:4 * l + 4]) for l in range(k)], "M": join(M[:]),
+            "k18": list(k18), "k36": list(k36), "bm": list(bm)}
 
 
 def wait_selftest(device=None):

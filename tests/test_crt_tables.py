@@ -1,0 +1,81 @@
+"""Number theory of the tensor-core FP64 engine, on the tables exactly as the
+library copies them to the device (host-only, no GPU): the moduli are
+pairwise coprime and small enough for exact FP16 residues and exact FP32
+chunk sums, their product leaves the margin the reconstruction relies on, the
+CRT weights form the idempotent basis, the limb weights and Barrett
+constants are what their definitions say, and reconstruction from residues
+returns every integer in the engine's range."""
+import math
+import random
+
+import numpy as np
+import pytest
+
+from paper_1207_1773_gb300 import gbhegv
+
+KMAX = 1 << 16        # largest contraction the engine accepts
+VMAX = 1 << 52        # operands are scaled to integers |v| <= 2^52
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_1207_1773_gb300 import build
+    build.build()
+    return gbhegv.crt_tables()
+
+
+def test_moduli(T):
+    p = T["p"]
+    assert len(p) == 16 and len(set(p)) == 16
+    assert all(2 <= x <= 256 for x in p)
+    for i in range(16):
+        for j in range(i + 1, 16):
+            assert math.gcd(p[i], p[j]) == 1, (p[i], p[j])
+    # symmetric residues |r| <= 128 are exact in FP16 (11-bit significand)
+    assert max(p) // 2 <= 2048
+    # a chunk of 512 products |r r'| <= 128^2 sums below 2^23: exact in FP32
+    assert 512 * (max(p) // 2) ** 2 <= 1 << 23
+
+
+def test_product_and_margin(T):
+    M = math.prod(T["p"])
+    assert T["M"] == M
+    # complex: |Re C|, |Im C| <= K * 2 * VMAX^2 = K 2^105, and this must stay below M / 8
+    assert 8 * KMAX * 2 * VMAX * VMAX < M
+
+
+def test_crt_basis(T):
+    p, W, M = T["p"], T["W"], T["M"]
+    for l, Wl in enumerate(W):
+        assert 0 <= Wl < M
+        for j, pj in enumerate(p):
+            assert Wl % pj == (1 if j == l else 0), (l, j)
+
+
+def test_limb_weights_and_barrett(T):
+    for pl, k18, k36, bm in zip(T["p"], T["k18"], T["k36"], T["bm"]):
+        assert k18 == pow(2, 18, pl) and k36 == pow(2, 36, pl)
+        assert bm == (1 << 32) // pl
+    # the Barrett quotient of a 32-bit x is floor(x / p) or one less
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.integers(0, 1 << 32, 20000, dtype=np.uint64),
+                         np.array([0, 1, (1 << 32) - 1], dtype=np.uint64)])
+    for pl, bm in zip(T["p"], T["bm"]):
+        q = (xs * np.uint64(bm)) >> np.uint64(32)
+        r = xs - q * np.uint64(pl)
+        assert np.all(r < np.uint64(2 * pl))
+
+
+def test_reconstruction_roundtrip(T):
+    p, W, M = T["p"], T["W"], T["M"]
+    bound = KMAX * 2 * VMAX * VMAX
+    rnd = random.Random(1)
+    cases = [0, 1, -1, bound, -bound] + [rnd.randint(-bound, bound) for _ in range(2000)]
+    for C in cases:
+        res = [C % pl for pl in p]
+        res = [r - pl if r > pl // 2 else r for r, pl in zip(res, p)]   # symmetric residues
+        assert all(abs(r) <= 128 for r in res)
+        s = sum(r * Wl for r, Wl in zip(res, W)) % M
+        if s > M // 2:
+            s -= M
+        assert s == C
