@@ -1270,11 +1270,13 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
 
 }  // namespace gbhe
 
-extern "C" int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, unsigned* k18, unsigned* k36, unsigned* bm) {
+extern "C" int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, unsigned* k18, unsigned* k36, unsigned* bm,
+                               float* frac) {
   gbhe::HostTables t;
   gbhe::crt_tables(t);
   for (int l = 0; l < gbhe::NMOD; ++l) {
     if (p) p[l] = t.p[l];
+    if (frac) frac[l] = t.frac[l];
     if (k18) k18[l] = t.k18[l];
     if (k36) k36[l] = t.k36[l];
     if (bm) bm[l] = t.bm[l];

@@ -55,7 +55,7 @@ def _load():
             "gbhe_set_workspace": ([P, P, S], I),
             "gbhe_get_status": ([P, P], I),
             "gbhe_sync_status": ([P, P], I),
-            "gbhe_crt_tables": ([P, P, P, P, P, P], I),
+            "gbhe_crt_tables": ([P, P, P, P, P, P, P], I),
             "gbhe_default_nb": ([I], I),
             "gbhe_potrf": ([P, I, P, I, P], I),
             "gbhe_hegst": ([P, I, P, I, P, I, P], I),
@@ -341,13 +341,15 @@ PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc"
 
 def crt_tables():
     """The tensor-core FP64 engine's tables (host-only): dict of p, W, M, k18,
-    k36, bm as Python ints (W and M joined from their 32-bit words)."""
+    k36, bm as Python ints (W and M joined from their 32-bit words) and frac
+    as the float32 values the device uses."""
     k = 16
     p = (ctypes.c_int * k)()
     W = (ctypes.c_uint * (4 * k))()
     M = (ctypes.c_uint * 4)()
     k18, k36, bm = (ctypes.c_uint * k)(), (ctypes.c_uint * k)(), (ctypes.c_uint * k)()
-    nmod = _load().gbhe_crt_tables(p, W, M, k18, k36, bm)
+    frac = (ctypes.c_float * k)()
+    nmod = _load().gbhe_crt_tables(p, W, M, k18, k36, bm, frac)
     if nmod != k:
         raise RuntimeError("unexpected number of moduli %d" % nmod)
 
@@ -355,7 +357,7 @@ def crt_tables():
         return sum(int(x) << (32 * i) for i, x in enumerate(words))
 
     return {"p": list(p), "W": [join(W[4 * l:4 * l + 4]) for l in range(k)], "M": join(M[:]),
-            "k18": list(k18), "k36": list(k36), "bm": list(bm)}
+            "k18": list(k18), "k36": list(k36), "bm": list(bm), "frac": list(frac)}
 
 
 def wait_selftest(device=None):

@@ -79,3 +79,36 @@ def test_reconstruction_roundtrip(T):
         if s > M // 2:
             s -= M
         assert s == C
+
+
+def _fmaf(a, b, c):
+    """float32 fused multiply-add: a*b + c is exact in float64 for a an 8-bit
+    integer, b and c float32 below 2^12 (fewer than 53 significant bits), so
+    one rounding to float32 gives the fused result."""
+    return np.float32(float(a) * float(b) + float(c))
+
+
+def test_quotient_estimate_and_160bit_reconstruction(T):
+    """The device sums unsigned residues c_l in [0, p_l): S = sum c_l W_l,
+    F = fmaf chain of c_l * frac_l (l = 0..15), q = rintf(F), C = S - q M.
+    Over the engine's whole range this returns C exactly; the FP32 estimate
+    stays within 2^-8 of the exact sum_l c_l y_l / p_l."""
+    p, W, M, frac = T["p"], T["W"], T["M"], T["frac"]
+    y = [(pow(M // pl, -1, pl)) for pl in p]
+    for l, pl in enumerate(p):
+        assert frac[l] == np.float32(y[l] / pl)
+    bound = KMAX * 2 * VMAX * VMAX
+    rnd = random.Random(2)
+    cases = [0, 1, -1, bound, -bound, bound - 1, -bound + 1] + [rnd.randint(-bound, bound) for _ in range(3000)]
+    worst = 0.0
+    for C in cases:
+        cv = [C % pl for pl in p]
+        F = np.float32(0.0)
+        for l in range(16):
+            F = _fmaf(np.float32(cv[l]), np.float32(frac[l]), F)
+        exact = sum(c * yl / pl for c, yl, pl in zip(cv, y, p))
+        worst = max(worst, abs(float(F) - exact))
+        q = int(np.rint(F))                      # round half to even, as rintf
+        S = sum(c * Wl for c, Wl in zip(cv, W))
+        assert S - q * M == C, C
+    assert worst < 2.0 ** -8, worst
