@@ -112,3 +112,30 @@ def test_quotient_estimate_and_160bit_reconstruction(T):
         S = sum(c * Wl for c, Wl in zip(cv, W))
         assert S - q * M == C, C
     assert worst < 2.0 ** -8, worst
+
+
+def test_residue_split_replay(T):
+    """The device's residue of a scaled integer |v| <= 2^52: three 18-bit
+    limbs (a, b, c), t = a (2^36 mod p) + b (2^18 mod p) + c, one Barrett
+    step with floor(2^32 / p) and one conditional subtraction, symmetric
+    representative, sign applied.  t stays below 2^32 (no 32-bit overflow),
+    and the result is v mod p with |r| <= 128."""
+    rng = np.random.default_rng(3)
+    top = 1 << 52
+    # largest magnitude that the rounding to 52 bits can produce: (2^53 - 1 + 1) >> 1
+    assert ((1 << 53) - 1 + 1) >> 1 == top
+    mags = [0, 1, top, top - 1, (1 << 36) - 1, 1 << 36, (1 << 18) - 1] + \
+        [int(x) for x in rng.integers(0, top, 5000, dtype=np.int64)]
+    for pl, k18, k36, bm in zip(T["p"], T["k18"], T["k36"], T["bm"]):
+        for mag in mags:
+            a, b, c = mag >> 36, (mag >> 18) & 0x3FFFF, mag & 0x3FFFF
+            t = a * k36 + b * k18 + c
+            assert t < 1 << 32
+            rr = t - ((t * bm) >> 32) * pl
+            assert 0 <= rr < 2 * pl
+            if rr >= pl:
+                rr -= pl
+            sv = rr - pl if rr > pl // 2 else rr
+            assert abs(sv) <= 128
+            for sign in (1, -1):
+                assert (sign * sv - sign * mag) % pl == 0
