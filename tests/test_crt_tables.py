@@ -139,3 +139,64 @@ def test_residue_split_replay(T):
             assert abs(sv) <= 128
             for sign in (1, -1):
                 assert (sign * sv - sign * mag) % pl == 0
+
+
+def _int160_to_double(C, sc):
+    """Replay of the device's 160-bit two's-complement integer -> double
+    conversion (leading word and two below it, sticky bit for the rest,
+    round to nearest even, carry into a new bit, scale 2^sc, flush below the
+    normal range)."""
+    M64 = (1 << 64) - 1
+    D = [(C >> (32 * i)) & 0xFFFFFFFF for i in range(5)]   # two's complement words
+    negv = D[4] >= 1 << 31
+    if negv:
+        v = (-C) & ((1 << 160) - 1)
+        D = [(v >> (32 * i)) & 0xFFFFFFFF for i in range(5)]
+    for top in (4, 3, 2, 1, 0):
+        if D[top]:
+            break
+    else:
+        return 0.0
+    t2 = D[top]
+    t1 = D[top - 1] if top >= 1 else 0
+    t0 = D[top - 2] if top >= 2 else 0
+    sticky = any(D[i] for i in range(0, max(top - 2, 0)))
+    lz = 32 - t2.bit_length()
+    hi = (t2 << 32) | t1
+    lo = (t0 << 32) & M64
+    if lz:
+        hi = ((hi << lz) | (lo >> (64 - lz))) & M64
+        lo = (lo << lz) & M64
+    sticky = sticky or lo != 0
+    mant, rem = hi >> 11, hi & 0x7FF
+    if rem > 0x400 or (rem == 0x400 and (sticky or mant & 1)):
+        mant += 1
+        if mant == 1 << 53:
+            mant >>= 1
+            sc += 1
+    e2 = 32 * top + 31 - lz - 52 + sc
+    expo = e2 + 52 + 1023
+    if expo <= 0:
+        return 0.0
+    if expo >= 2047:
+        return -math.inf if negv else math.inf
+    return math.ldexp(-mant if negv else mant, e2)
+
+
+def test_int160_to_double_rounds_once_to_nearest_even():
+    rnd = random.Random(4)
+    cases = [1, -1, 2, (1 << 53) - 1, 1 << 53, (1 << 53) + 1, (1 << 54) + 2, (1 << 54) + 6,
+             (1 << 127) - 1, -(1 << 127), (1 << 159) - 1, -(1 << 159)]
+    for _ in range(3000):
+        k = rnd.randint(54, 150)
+        m = rnd.getrandbits(53) | (1 << 52)
+        s = k - 53
+        base = m << s
+        half = 1 << (s - 1)
+        cases += [base, base + half, base + half - 1, base + half + 1, base - 1, rnd.getrandbits(k)]
+    for C in cases:
+        for v in (C, -C):
+            if not -(1 << 159) <= v < 1 << 159:
+                continue
+            assert _int160_to_double(v, 0) == float(v), v
+            assert _int160_to_double(v, -104) == math.ldexp(float(v), -104), v
