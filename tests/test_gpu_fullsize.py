@@ -1,6 +1,9 @@
 """Parity at the workloads' full sizes: the n = 4096 pair (all eigenpairs,
-lowest 25 %, lowest 10 %) and the n = 10000 pair in the launch configuration
-the benchmark times (all eigenpairs, nb = 64).  The oracle cannot run at these
+lowest 25 %, lowest 10 %), the n = 10000 pair in the launch configuration
+the benchmark times (all eigenpairs, nb = 64), and -- only with GBHE_CFG2=1,
+since it needs about 100 GB of device and 25 GB of host memory -- the
+n = 20000 pair with a clustered spectrum and an ill-conditioned B (all
+eigenpairs and the lowest 20 %).  The oracle cannot run at these
 sizes inside a test, so the checks are properties that hold at any size:
 
   * eigenvalues against the constructed spectrum Lambda (known exactly):
@@ -10,6 +13,8 @@ sizes inside a test, so the checks are properties that hold at any size:
     B-orthonormality ||X^H B X - I||_F / (n eps) <= 100 on 64 sampled columns
     (both products formed with torch on the device; test arithmetic only).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -28,9 +33,9 @@ def G():
     return gbhegv
 
 
-def _pair(n, seed):
+def _pair(n, seed, kind="uniform", lo=-10.0, hi=10.0, ldiag="abs_normal"):
     from paper_1207_1773_gb300 import inputs
-    A, B, lam = inputs.make_pair(n, seed, "uniform", -10.0, 10.0, device=torch.device(DEV))
+    A, B, lam = inputs.make_pair(n, seed, kind, lo, hi, ldiag=ldiag, device=torch.device(DEV))
     A0 = torch.from_numpy(A).to(DEV).t().contiguous().t()
     B0 = torch.from_numpy(B).to(DEV).t().contiguous().t()
     return A0, B0, lam
@@ -72,3 +77,18 @@ def test_hegv_n10000_bench_config(G):
     A0, B0, lam = _pair(10000, 10)
     ev = torch.linalg.eigvalsh(B0).cpu().numpy()
     _check(G, A0, B0, lam, 10000, 64, ev[-1] / ev[0])
+
+
+@pytest.fixture(scope="module")
+def pair20000():
+    return _pair(20000, 2, "clustered", -1.0, 1.0, ldiag="loguniform")
+
+
+@pytest.mark.skipif(os.environ.get("GBHE_CFG2") != "1",
+                    reason="n = 20000 workload (about 100 GB device, 25 GB host memory): set GBHE_CFG2=1")
+@pytest.mark.parametrize("frac", [1.0, 0.20])
+def test_hegv_n20000_clustered_illconditioned(G, pair20000, frac):
+    from paper_1207_1773_gb300 import inputs
+    A0, B0, lam = pair20000
+    ev = torch.linalg.eigvalsh(B0).cpu().numpy()
+    _check(G, A0, B0, lam, inputs.fraction_iu(20000, frac), 64, ev[-1] / ev[0])
