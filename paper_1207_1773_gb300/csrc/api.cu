@@ -76,7 +76,7 @@ size_t stage_bytes(gbhe_handle h, int n, int nb, int m) {
   return s;
 }
 
-// Outputs of the intermediate stages that the driver keeps in the workspace.
+// Outputs of the intermediate stages that gbhe_hegv keeps in the workspace.
 size_t driver_bytes(int n, int nb, int m) {
   const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max(m, 1);
   const size_t npan = (nn + nb - 1) / nb;
