@@ -122,20 +122,49 @@ def _check(fn, rc):
 
 
 def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    """Device address of a CUDA tensor (None gives NULL).  Host tensors are
+    refused: the library would read their addresses as device memory."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("gbhegv takes CUDA tensors only (got a %s tensor)" % t.device.type)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+C128, F64 = torch.complex128, torch.float64
+
+
+def _want(dtype, device, *ts):
+    """Every tensor is a CUDA tensor of `dtype` on `device` (the library reads
+    each as that element type on the handle's device)."""
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("gbhegv takes CUDA tensors only (got a %s tensor)" % t.device.type)
+        if t.dtype != dtype:
+            raise TypeError("gbhegv: expected %s, got %s" % (dtype, t.dtype))
+        if t.device != device:
+            raise ValueError("gbhegv: tensors on %s and %s" % (device, t.device))
 
 
 def _stream(dev):
     return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
 
 
+def _cuda_device(device):
+    """torch.device of a CUDA device with its index (None: the current one)."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    if dev.type != "cuda":
+        raise ValueError("gbhegv runs on CUDA devices only")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    return dev
+
+
 class Handle:
     """A library handle on one device plus a torch-allocated workspace."""
 
     def __init__(self, device=None):
-        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        if dev.type != "cuda":
-            raise ValueError("gbhegv runs on CUDA devices only")
+        dev = _cuda_device(device)
         self.device = dev
         lib = _load()
         h = ctypes.c_void_p()
@@ -215,8 +244,8 @@ _handles = {}
 
 
 def handle(device=None) -> Handle:
-    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    key = dev.index or 0
+    dev = _cuda_device(device)
+    key = dev.index
     if key not in _handles:
         _handles[key] = Handle(dev)
     return _handles[key]
@@ -252,6 +281,7 @@ def _sync_status(h, fn):
 # ----------------------------------------------------------------- stages
 def potrf(B, check=True):
     h = handle(B.device)
+    _want(C128, B.device, B)
     n = B.shape[0]
     h.ensure_workspace(n)
     _check("gbhe_potrf", _load().gbhe_potrf(h.h, n, _ptr(B), _ld(B), _stream(B.device)))
@@ -260,6 +290,7 @@ def potrf(B, check=True):
 
 def hegst(A, L):
     h = handle(A.device)
+    _want(C128, A.device, A, L)
     n = A.shape[0]
     h.ensure_workspace(n)
     _check("gbhe_hegst", _load().gbhe_hegst(h.h, n, _ptr(A), _ld(A), _ptr(L), _ld(L), _stream(A.device)))
@@ -268,6 +299,7 @@ def hegst(A, L):
 def he2hb(A, nb):
     """Returns (T1, tau1); A is overwritten by band + V1."""
     h = handle(A.device)
+    _want(C128, A.device, A)
     n = A.shape[0]
     h.ensure_workspace(n, nb)
     npan = max((n + nb - 1) // nb, 1)
@@ -287,6 +319,7 @@ def hb2st_sizes(n, nb):
 def hb2st(A, nb):
     """Returns (d, e, V2, tau2) from the lower band of A."""
     h = handle(A.device)
+    _want(C128, A.device, A)
     n = A.shape[0]
     h.ensure_workspace(n, nb)
     nv, nt = hb2st_sizes(n, nb)
@@ -303,6 +336,7 @@ def hb2st(A, nb):
 def stedc(d, e, il=1, iu=None):
     """Eigenpairs il..iu of the real symmetric tridiagonal (d, e): (w, Z)."""
     h = handle(d.device)
+    _want(F64, d.device, d, e)
     n = d.shape[0]
     iu = n if iu is None else iu
     m = iu - il + 1
@@ -318,6 +352,8 @@ def stedc(d, e, il=1, iu=None):
 
 def unmtr_2stage(nb, A, T1, V2, tau2, Z):
     h = handle(A.device)
+    _want(C128, A.device, A, T1, V2, tau2)
+    _want(F64, A.device, Z)
     n, m = Z.shape
     h.ensure_workspace(n, nb, m)
     X = torch.zeros((max(m, 1), n), dtype=torch.complex128, device=A.device).t()
@@ -330,6 +366,7 @@ def unmtr_2stage(nb, A, T1, V2, tau2, Z):
 
 def trsm_lh(L, X):
     h = handle(L.device)
+    _want(C128, L.device, L, X)
     n, m = X.shape
     h.ensure_workspace(n, 0, m)
     _check("gbhe_trsm_lh", _load().gbhe_trsm_lh(h.h, n, m, _ptr(L), _ld(L), _ptr(X), _ld(X), _stream(L.device)))
@@ -417,6 +454,7 @@ def set_crt_block(block=16384, device=None):
 def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     """C = alpha op(A) op(B) + beta C through the library's GEMM engine (in place)."""
     h = handle(C.device)
+    _want(C128, C.device, A, B, C)
     m, n = C.shape
     k = A.shape[1] if opA in ("N", "H") else A.shape[0]
     h.ensure_workspace(max(m, n, k), 1, 1)
@@ -431,6 +469,7 @@ def zgemm_static(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     """C = alpha op(A) op(B) + beta C on the DMMA GEMM with split-K scratch in
     the library's static array (no handle, no workspace), in place.  Calls
     must not overlap in time on one device; m * n <= 2**18."""
+    _want(C128, C.device, A, B, C)
     m, n = C.shape
     k = A.shape[1] if opA in ("N", "H") else A.shape[0]
     a, b = complex(alpha), complex(beta)
@@ -446,6 +485,9 @@ def gemm_crt(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     """C = alpha op(A) op(B) + beta C computed exactly-modularly on the FP16
     tensor cores (complex128 or float64 operands), in place."""
     h = handle(C.device)
+    if C.dtype not in (C128, F64):
+        raise TypeError("gbhegv: expected complex128 or float64, got %s" % C.dtype)
+    _want(C.dtype, C.device, A, B, C)
     cplx = 1 if C.dtype == torch.complex128 else 0
     m, n = C.shape
     k = A.shape[1] if opA in ("N", "H") else A.shape[0]
@@ -466,6 +508,8 @@ def hegv_adjoint(w_all, X_all, il, iu, gw, gX, delta):
     n = X_all.shape[0]
     m = iu - il + 1
     h = handle(X_all.device)
+    _want(F64, X_all.device, w_all, gw)
+    _want(C128, X_all.device, X_all, gX)
     h.ensure_workspace(n, 0, m)
     dA = torch.empty((n, n), dtype=torch.complex128, device=X_all.device).t()
     dB = torch.empty((n, n), dtype=torch.complex128, device=X_all.device).t()
@@ -481,7 +525,7 @@ def _int_array(vals):
 
 
 def _ptr_array(ts):
-    return (ctypes.c_void_p * max(len(ts), 1))(*[t.data_ptr() for t in ts])
+    return (ctypes.c_void_p * max(len(ts), 1))(*[_ptr(t).value for t in ts])
 
 
 def batched_plan(ns, nworkers):
@@ -496,7 +540,7 @@ class BatchPool:
     hegv_batched; sized by prepare() for a set of problem shapes."""
 
     def __init__(self, nworkers=4, device=None):
-        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        dev = _cuda_device(device)
         self.device = dev
         self.handles = [Handle(dev) for _ in range(nworkers)]
         self.streams = [torch.cuda.Stream(dev) for _ in range(nworkers)]
@@ -519,6 +563,8 @@ def hegv_batched(pool, As, Bs, ils, ius, nbs, ws, Xs):
     (overwritten), the eigenvalue vectors ws[i] and the eigenvector blocks
     Xs[i] (n_i x m_i, column-major) are caller-owned CUDA tensors."""
     cnt = len(As)
+    _want(C128, pool.device, *As, *Bs, *Xs)
+    _want(F64, pool.device, *ws)
     ns = [a.shape[0] for a in As]
     hs = (ctypes.c_void_p * len(pool.handles))(*[h.h.value for h in pool.handles])
     strm = (ctypes.c_void_p * len(pool.streams))(*[s.cuda_stream for s in pool.streams])
@@ -535,6 +581,7 @@ def hegv(A, B, il=1, iu=None, nb=0, onestage=False, check=True):
     A, B: column-major complex128 CUDA tensors (lower triangles read), both
     overwritten.  Returns (w, X) with X B-orthonormal."""
     h = handle(A.device)
+    _want(C128, A.device, A, B)
     n = A.shape[0]
     iu = n if iu is None else iu
     m = iu - il + 1

@@ -1,0 +1,68 @@
+"""The Python binding fails loudly instead of falling back (no GPU needed):
+CPU tensors are refused before any work, row-major matrices are refused, and
+a missing library raises instead of importing any other implementation."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1207_1773_gb300 import gbhegv  # noqa: E402
+
+
+def test_cpu_tensors_are_refused():
+    A = torch.eye(4, dtype=torch.complex128).t()
+    B = torch.eye(4, dtype=torch.complex128).t()
+    with pytest.raises(ValueError, match="CUDA"):
+        gbhegv.hegv(A, B)
+    with pytest.raises(ValueError, match="CUDA"):
+        gbhegv.Handle("cpu")
+
+
+def test_row_major_is_refused():
+    X = torch.zeros((3, 5), dtype=torch.complex128)   # row-major, stride (5, 1)
+    with pytest.raises(ValueError, match="column-major"):
+        gbhegv._ld(X)
+    assert gbhegv._ld(X.t().contiguous().t()) == 3
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    monkeypatch.setattr(gbhegv, "_lib", None)
+    monkeypatch.setattr(gbhegv, "_LIBPATH", str(tmp_path / "libgbhegv.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        gbhegv._load()
+    with pytest.raises(RuntimeError, match="not built"):
+        gbhegv.nb_rule_pick([], 100)
+
+
+def test_host_device_never_maps_to_a_cached_gpu_handle(monkeypatch):
+    """A CPU tensor must not pick up the handle cached for GPU 0: its host
+    address would reach the GPU kernels."""
+    monkeypatch.setattr(gbhegv, "_handles", {0: object()})
+    with pytest.raises(ValueError, match="CUDA"):
+        gbhegv.handle("cpu")
+    with pytest.raises(ValueError, match="CUDA"):
+        gbhegv.hegv(torch.eye(2, dtype=torch.complex128), torch.eye(2, dtype=torch.complex128))
+
+
+class _FakeCuda:
+    """Stands in for a CUDA tensor in the host-side argument checks."""
+
+    def __init__(self, dtype, device="cuda:0"):
+        self.is_cuda = True
+        self.dtype = dtype
+        self.device = torch.device(device)
+
+
+def test_element_type_and_device_are_checked():
+    dev = torch.device("cuda:0")
+    gbhegv._want(torch.complex128, dev, _FakeCuda(torch.complex128))
+    with pytest.raises(TypeError, match="complex128"):
+        gbhegv._want(torch.complex128, dev, _FakeCuda(torch.complex64))
+    with pytest.raises(TypeError):
+        gbhegv._want(torch.float64, dev, _FakeCuda(torch.float32))
+    with pytest.raises(ValueError, match="cuda:1"):
+        gbhegv._want(torch.complex128, dev, _FakeCuda(torch.complex128, "cuda:1"))
+    with pytest.raises(ValueError, match="CUDA"):
+        gbhegv._want(torch.float64, dev, torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        gbhegv._ptr(torch.zeros(3))
+    assert gbhegv._ptr(None) is None
