@@ -134,6 +134,21 @@ def _ptr(t):
 C128, F64 = torch.complex128, torch.float64
 
 
+def _square(*ts):
+    """All are n x n matrices with one n; returns n."""
+    n = ts[0].shape[0] if ts[0].dim() == 2 else -1
+    for t in ts:
+        if t.dim() != 2 or t.shape[0] != n or t.shape[1] != n:
+            raise ValueError("gbhegv: expected %d x %d matrices, got %s" % (n, n, tuple(t.shape)))
+    return n
+
+
+def _block(t, n, m, name):
+    """t holds an n x m column-major block (at least)."""
+    if t.dim() != 2 or t.shape[0] != n or t.shape[1] < m:
+        raise ValueError("gbhegv: %s must be %d x %d, got %s" % (name, n, m, tuple(t.shape)))
+
+
 def _want(dtype, device, *ts):
     """Every tensor is a CUDA tensor of `dtype` on `device` (the library reads
     each as that element type on the handle's device)."""
@@ -282,7 +297,7 @@ def _sync_status(h, fn):
 def potrf(B, check=True):
     h = handle(B.device)
     _want(C128, B.device, B)
-    n = B.shape[0]
+    n = _square(B)
     h.ensure_workspace(n)
     _check("gbhe_potrf", _load().gbhe_potrf(h.h, n, _ptr(B), _ld(B), _stream(B.device)))
     return h.status() if check else 0
@@ -291,7 +306,7 @@ def potrf(B, check=True):
 def hegst(A, L):
     h = handle(A.device)
     _want(C128, A.device, A, L)
-    n = A.shape[0]
+    n = _square(A, L)
     h.ensure_workspace(n)
     _check("gbhe_hegst", _load().gbhe_hegst(h.h, n, _ptr(A), _ld(A), _ptr(L), _ld(L), _stream(A.device)))
 
@@ -300,7 +315,7 @@ def he2hb(A, nb):
     """Returns (T1, tau1); A is overwritten by band + V1."""
     h = handle(A.device)
     _want(C128, A.device, A)
-    n = A.shape[0]
+    n = _square(A)
     h.ensure_workspace(n, nb)
     npan = max((n + nb - 1) // nb, 1)
     T1 = torch.zeros(npan * nb * nb, dtype=torch.complex128, device=A.device)
@@ -320,7 +335,7 @@ def hb2st(A, nb):
     """Returns (d, e, V2, tau2) from the lower band of A."""
     h = handle(A.device)
     _want(C128, A.device, A)
-    n = A.shape[0]
+    n = _square(A)
     h.ensure_workspace(n, nb)
     nv, nt = hb2st_sizes(n, nb)
     d = torch.zeros(max(n, 1), dtype=torch.float64, device=A.device)
@@ -355,6 +370,8 @@ def unmtr_2stage(nb, A, T1, V2, tau2, Z):
     _want(C128, A.device, A, T1, V2, tau2)
     _want(F64, A.device, Z)
     n, m = Z.shape
+    if _square(A) != n:
+        raise ValueError("gbhegv: Z must have %d rows, got %d" % (A.shape[0], n))
     h.ensure_workspace(n, nb, m)
     X = torch.zeros((max(m, 1), n), dtype=torch.complex128, device=A.device).t()
     _check("gbhe_unmtr_2stage", _load().gbhe_unmtr_2stage(h.h, n, nb, m, _ptr(A), _ld(A), _ptr(T1), _ptr(V2),
@@ -368,6 +385,8 @@ def trsm_lh(L, X):
     h = handle(L.device)
     _want(C128, L.device, L, X)
     n, m = X.shape
+    if _square(L) != n:
+        raise ValueError("gbhegv: X must have %d rows, got %d" % (L.shape[0], n))
     h.ensure_workspace(n, 0, m)
     _check("gbhe_trsm_lh", _load().gbhe_trsm_lh(h.h, n, m, _ptr(L), _ld(L), _ptr(X), _ld(X), _stream(L.device)))
 
@@ -565,6 +584,14 @@ def hegv_batched(pool, As, Bs, ils, ius, nbs, ws, Xs):
     cnt = len(As)
     _want(C128, pool.device, *As, *Bs, *Xs)
     _want(F64, pool.device, *ws)
+    if not len(Bs) == len(Xs) == len(ws) == len(ils) == len(ius) == len(nbs) == cnt:
+        raise ValueError("gbhegv: one entry per problem in every list")
+    for a, b, x, w, il, iu in zip(As, Bs, Xs, ws, ils, ius):
+        n = _square(a, b)
+        m = max(iu - il + 1, 0)
+        _block(x, n, m, "X_i")
+        if w.numel() < m:
+            raise ValueError("gbhegv: w_i holds %d values, needs %d" % (w.numel(), m))
     ns = [a.shape[0] for a in As]
     hs = (ctypes.c_void_p * len(pool.handles))(*[h.h.value for h in pool.handles])
     strm = (ctypes.c_void_p * len(pool.streams))(*[s.cuda_stream for s in pool.streams])
@@ -582,7 +609,7 @@ def hegv(A, B, il=1, iu=None, nb=0, onestage=False, check=True):
     overwritten.  Returns (w, X) with X B-orthonormal."""
     h = handle(A.device)
     _want(C128, A.device, A, B)
-    n = A.shape[0]
+    n = _square(A, B)
     iu = n if iu is None else iu
     m = iu - il + 1
     nbu = nb if nb else (h.resolve_nb(n, m) if 0 <= m <= n else _load().gbhe_default_nb(n))

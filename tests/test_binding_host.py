@@ -66,3 +66,19 @@ def test_element_type_and_device_are_checked():
     with pytest.raises(ValueError, match="CUDA"):
         gbhegv._ptr(torch.zeros(3))
     assert gbhegv._ptr(None) is None
+
+
+def test_shapes_are_checked():
+    sq = torch.zeros((4, 4), dtype=torch.complex128)
+    assert gbhegv._square(sq, sq) == 4
+    with pytest.raises(ValueError, match="4 x 4"):
+        gbhegv._square(sq, torch.zeros((3, 3), dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        gbhegv._square(torch.zeros((4, 3), dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        gbhegv._square(torch.zeros(4, dtype=torch.complex128))
+    gbhegv._block(torch.zeros((4, 2)), 4, 2, "X")
+    with pytest.raises(ValueError, match="X must be 4 x 3"):
+        gbhegv._block(torch.zeros((4, 2)), 4, 3, "X")
+    with pytest.raises(ValueError):
+        gbhegv._block(torch.zeros((5, 3)), 4, 3, "X")
