@@ -200,3 +200,29 @@ def test_int160_to_double_rounds_once_to_nearest_even():
                 continue
             assert _int160_to_double(v, 0) == float(v), v
             assert _int160_to_double(v, -104) == math.ldexp(float(v), -104), v
+
+
+def _crt_ws(m, n, k, cplx):
+    import ctypes
+    out = ctypes.c_size_t()
+    rc = gbhegv._load().gbhe_crt_workspace_size(m, n, k, cplx, ctypes.byref(out))
+    return rc, out.value
+
+
+def test_crt_workspace_matches_the_layout(T):
+    """Residue planes 16 x (Re, Im) x rows x K padded to 32 (FP16) for both
+    operands, output residue bytes in 128 x 64 tiles per modulus and
+    component, one exponent per row and column, plus alignment."""
+    for m, n, k, cplx in [(1, 1, 1, 1), (128, 64, 32, 0), (129, 65, 33, 1), (4096, 4096, 64, 1),
+                          (10000, 10000, 10000, 1), (300, 7000, 65536, 0)]:
+        nc = 2 if cplx else 1
+        kp = -(-k // 32) * 32
+        tiles = -(-m // 128) * -(-n // 64)
+        want = 16 * nc * (m + n) * kp * 2 + tiles * 16 * nc * 128 * 64 + (m + n) * 4 + 4 * 256
+        rc, got = _crt_ws(m, n, k, cplx)
+        assert rc == 0 and got == want, (m, n, k, cplx, got, want)
+    # about 16 GB for one complex product of order 10000 in every dimension
+    assert abs(_crt_ws(10000, 10000, 10000, 1)[1] / 1e9 - 16.1) < 0.1
+    assert _crt_ws(-1, 1, 1, 1)[0] == -1
+    assert _crt_ws(1, -1, 1, 1)[0] == -2
+    assert _crt_ws(1, 1, 65537, 1)[0] == -3          # beyond the exactness bound K <= 2^16
