@@ -76,3 +76,53 @@ def test_product_path_has_no_oracle_import():
                 src = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "oracle.c" not in src, f
+
+
+_C_PROGRAM = r"""
+#include <stdio.h>
+#include "gbhegv.h"
+#include "gbhegv_probe.h"
+int main(void) {
+  int nm[2] = {500, 4000}, nb[2] = {32, 64}, out = 0, p[16], assign[3], ns[3] = {100, 300, 200}, rc;
+  double fm[2] = {1.0, 1.0};
+  unsigned W[64], M[4];
+  size_t v2 = 0, t2 = 0, ws = 0;
+  rc = gbhe_nb_rule_pick(2, nm, fm, nb, 3000, 300, &out);
+  printf("%d %d\n", rc, out);
+  rc = gbhe_crt_tables(p, W, M, NULL, NULL, NULL, NULL);
+  printf("%d %d\n", rc, p[0]);
+  rc = gbhe_batched_plan(2, 3, ns, assign);
+  printf("%d %d %d %d\n", rc, assign[0], assign[1], assign[2]);
+  rc = gbhe_hb2st_sizes(100, 16, &v2, &t2);
+  printf("%d %zu %zu\n", rc, v2, t2);
+  rc = gbhe_crt_workspace_size(128, 64, 32, 0, &ws);
+  printf("%d %zu\n", rc, ws);
+  printf("%d %s\n", gbhe_default_nb(10000), gbhe_status_string(GBHE_ETIMEOUT));
+  return 0;
+}
+"""
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_header_is_plain_c_and_links(lib, tmp_path, compiler, std):
+    """The public headers compile as C99 and as C++ (extern "C") without
+    warnings, and a C program links libgbhegv.so and calls its host-only
+    entry points."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(compiler + " not found")
+    src = tmp_path / ("t.c" if compiler == "gcc" else "t.cpp")
+    src.write_text(_C_PROGRAM)
+    libdir = os.path.join(ROOT, "paper_1207_1773_gb300")
+    exe = tmp_path / "t"
+    subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L" + libdir, "-lgbhegv", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    assert out[0] == "0 64"
+    assert out[1] == "16 256"
+    assert out[2] == "0 1 0 1"                 # 300 -> worker 0, 200 -> worker 1, 100 -> worker 1
+    J = (100 - 1 + 15) // 16
+    assert out[3] == "0 %d %d" % (100 * J * 16, 100 * J)
+    assert out[4].split()[0] == "0" and int(out[4].split()[1]) > 0
+    assert out[5] == "64 bounded device wait expired"
