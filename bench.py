@@ -54,6 +54,19 @@ def _load_peaks():
 PEAKS = _load_peaks()
 
 
+def chase_roofline(pc, hbm_gbs, dfma_tflops):
+    """The bulge chase against both candidate bounds: its bytes (band in and
+    out, reflectors written) over the HBM peak, and its flops over the FP64
+    FMA pipe (the real bound: about 190 flop per byte on a 2n-step chain)."""
+    if not pc or pc.get("ms", 0) <= 0:
+        return None
+    sec = pc["ms"] * 1e-3
+    gbs = pc.get("bytes", 0.0) / sec / 1e9
+    tf = pc.get("flops", 0.0) / sec / 1e12
+    return {"ms": pc["ms"], "hbm_gbs": gbs, "hbm_frac": gbs / hbm_gbs if hbm_gbs else None,
+            "fp64_tflops": tf, "dfma_frac": tf / dfma_tflops if dfma_tflops else None}
+
+
 def nominal_flops(n, m):
     return 32.0 / 3.0 * n ** 3 + 12.0 * n * n * m
 
@@ -377,6 +390,7 @@ def run_ours(args):
     classes = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                    "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 and v["flops"] > 0 else None}
                for k, v in prof.items() if v["launches"] > 0}
+    chase = chase_roofline(prof.get("chase"), PEAKS.get("hbm_gbs"), dfma_peak)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only), bounded sample
     cpu = None
@@ -408,6 +422,7 @@ def run_ours(args):
             "max_abs_eig_err": eig_err,
             "roofline": roof,
             "kernel_classes": classes,
+            "chase_roofline": chase,
             "fp64_peaks_tflops": {"dfma": dfma_peak, "dmma": dmma_peak},
             "cpu_baseline": cpu,
             "e2e": e2e,
