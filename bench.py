@@ -97,6 +97,8 @@ def parse():
     p.add_argument("--adjoint", action="store_true",
                    help="adjoint workload: n=2048 pair, lowest 64 eigenpairs, forward + backward vs forward alone")
     p.add_argument("--cache", default=None, help="directory to keep the generated input pair between runs")
+    p.add_argument("--stages", action="store_true",
+                   help="time each C-ABI stage alone at --n / --frac / --nb (one JSON line)")
     return p.parse_args()
 
 
@@ -648,12 +650,77 @@ def run_q2_case(args):
     return 0
 
 
+def run_stages(args):
+    """Each C-ABI stage of the two-stage solve timed alone (CUDA events around
+    the stage's call on the current stream; the stages' small output buffers
+    are allocated inside), after one untimed pass for the one-time set-ups:
+    times, FP64-equivalent rates from the nominal stage flops, and their
+    multiple of the live DMMA peak."""
+    import numpy as np
+    import torch
+
+    from paper_1207_1773_gb300 import gbhegv as G
+    from paper_1207_1773_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, nb = args.n, args.nb
+    m = max(1, inputs.fraction_iu(n, args.frac))
+    A_np, B_np, lam = inputs.make_pair(n, args.seed, "uniform", -10.0, 10.0, device=dev if n > 3000 else None)
+    A0, B0 = G.colmajor(A_np, dev), G.colmajor(B_np, dev)
+    dfma_peak, dmma_peak = G.probe_fp64_peaks(dev.index)
+    G.handle(dev).ensure_workspace(n, nb, m)
+    nominal = {"potrf": 4.0 / 3.0 * n ** 3, "hegst": 4.0 * n ** 3, "he2hb": 16.0 / 3.0 * n ** 3,
+               "hb2st": 24.0 * n * n * nb, "stedc": None, "unmtr_2stage": 16.0 * n * n * m, "trsm_lh": 4.0 * n * n * m}
+
+    def one_pass():
+        A = torch.empty_like(A0).copy_(A0)
+        B = torch.empty_like(B0).copy_(B0)
+        st = torch.cuda.current_stream(dev)
+        out, keep = {}, {}
+
+        def stage(name, fn):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(st)
+            r = fn()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            out[name] = e0.elapsed_time(e1) / 1e3
+            return r
+
+        info = stage("potrf", lambda: G.potrf(B))
+        if info != 0:
+            raise RuntimeError("potrf status %d" % info)
+        stage("hegst", lambda: G.hegst(A, B))
+        keep["T1"], _ = stage("he2hb", lambda: G.he2hb(A, nb))
+        d, e, keep["V2"], keep["tau2"] = stage("hb2st", lambda: G.hb2st(A, nb))
+        w, Z = stage("stedc", lambda: G.stedc(d, e, 1, m))
+        X = stage("unmtr_2stage", lambda: G.unmtr_2stage(nb, A, keep["T1"], keep["V2"], keep["tau2"], Z))
+        stage("trsm_lh", lambda: G.trsm_lh(B, X))
+        return out, w
+
+    one_pass()
+    times, w = one_pass()
+    stages = {}
+    for k, t in times.items():
+        f = nominal[k]
+        rate = f / t / 1e12 if f else None
+        stages[k] = {"s": round(t, 4), "tflops_fp64_equivalent": rate,
+                     "x_dmma_peak": rate / dmma_peak if rate else None}
+    print(json.dumps({"stages": stages, "total_s": sum(times.values()), "n": n, "m": m, "nb": nb,
+                      "max_abs_eig_err": float(np.max(np.abs(w.cpu().numpy() - lam[:m]))),
+                      "fp64_peaks_tflops": {"dfma": dfma_peak, "dmma": dmma_peak}}))
+    return 0
+
+
 def main():
     args = parse()
     if args.micro:
         return run_micro(args.micro)
     if args.q2_case:
         return run_q2_case(args)
+    if args.stages:
+        return run_stages(args)
     if args.batched:
         return run_batched(args)
     if args.adjoint:
