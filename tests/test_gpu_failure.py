@@ -10,7 +10,7 @@ import oracle
 from paper_1207_1773_gb300 import inputs
 
 torch = pytest.importorskip("torch")
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late]
 
 EPS = np.finfo(np.float64).eps
 DEV = "cuda:0"

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.last]
 EPS = np.finfo(np.float64).eps
 DEV = "cuda:0"
 
