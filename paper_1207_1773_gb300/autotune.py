@@ -48,9 +48,9 @@ def rule_from_timings(results):
 
 
 class GpuTimer:
-    """Seconds of one gbhe_hegv call (best of `reps` after one warm-up), CUDA
-    events on the current stream, on a fresh copy of the seeded pair each
-    time (the solve overwrites A and B)."""
+    """Seconds of one two-stage solve (best of `reps` after one warm-up), CUDA
+    events on the current stream around gbhegv.hegv, on a fresh copy of the
+    seeded pair each time (the solve overwrites A and B)."""
 
     def __init__(self, handle, seed=0, reps=2):
         self.h = handle
@@ -67,16 +67,11 @@ class GpuTimer:
         return self._pairs[n]
 
     def __call__(self, n, m, nb):
-        import ctypes
-
         import torch
         from . import gbhegv
-        lib = gbhegv._load()
         A0, B0 = self._pair(n)
         dev = self.h.device
-        self.h.ensure_workspace(n, nb, m)
-        w = torch.empty(m, dtype=torch.float64, device=dev)
-        X = torch.empty((m, n), dtype=torch.complex128, device=dev).t()
+        gbhegv.handle(dev).ensure_workspace(n, nb, m)
         st = torch.cuda.current_stream(dev)
         best = math.inf
         for r in range(self.reps + 1):
@@ -85,11 +80,11 @@ class GpuTimer:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            rc = lib.gbhe_hegv(self.h.h, n, nb, gbhegv._ptr(A), n, gbhegv._ptr(B), n, 1, m, gbhegv._ptr(w),
-                               gbhegv._ptr(X), n, ctypes.c_void_p(st.cuda_stream))
+            gbhegv.hegv(A, B, 1, m, nb=nb, check=False)
             e1.record(st)
-            gbhegv._check("gbhe_hegv", rc)
-            gbhegv._sync_status(self.h, "gbhe_hegv")
+            status = gbhegv.handle(dev).status()
+            if status != 0:
+                raise gbhegv.GbheError("gbhe_hegv", status)
             if r > 0:
                 best = min(best, e0.elapsed_time(e1) / 1e3)
         return best
