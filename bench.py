@@ -99,6 +99,8 @@ def parse():
     p.add_argument("--cache", default=None, help="directory to keep the generated input pair between runs")
     p.add_argument("--stages", action="store_true",
                    help="time each C-ABI stage alone at --n / --frac / --nb (one JSON line)")
+    p.add_argument("--cusolver", action="store_true",
+                   help="context: the same solve assembled from torch.linalg library calls at --n (one JSON line)")
     return p.parse_args()
 
 
@@ -713,6 +715,46 @@ def run_stages(args):
     return 0
 
 
+def run_cusolver(args):
+    """Context comparator on the same GPU: the generalized solve assembled from
+    library calls (torch.linalg on CUDA: Cholesky, two triangular solves for
+    L^-1 A L^-H, the Hermitian eigensolver, one triangular solve for X), all
+    eigenpairs, on the same seeded pair; one warm-up solve at n = 512 first."""
+    import numpy as np
+    import torch
+
+    from paper_1207_1773_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+
+    def solve(A, B):
+        L = torch.linalg.cholesky(B)
+        Y = torch.linalg.solve_triangular(L, A, upper=False)
+        Ap = torch.linalg.solve_triangular(L, Y.conj().transpose(0, 1), upper=False)
+        Ap = 0.5 * (Ap + Ap.conj().transpose(0, 1))
+        w, Z = torch.linalg.eigh(Ap)
+        X = torch.linalg.solve_triangular(L.conj().transpose(0, 1), Z, upper=True)
+        return w, X
+
+    a, b, _ = inputs.make_pair(512, 0)
+    solve(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
+    A_np, B_np, lam = inputs.make_pair(n, args.seed, "uniform", -10.0, 10.0, device=dev if n > 3000 else None)
+    A, B = torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    w, _ = solve(A, B)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3
+    print(json.dumps({"comparator": "library pipeline (torch.linalg on CUDA: cholesky, solve_triangular, eigh)",
+                      "n": n, "m": n, "solve_time_s": t, "value": nominal_flops(n, n) / t / 1e9, "unit": UNIT,
+                      "max_abs_eig_err": float(np.max(np.abs(w.cpu().numpy() - lam)))}))
+    return 0
+
+
 def main():
     args = parse()
     if args.micro:
@@ -721,6 +763,8 @@ def main():
         return run_q2_case(args)
     if args.stages:
         return run_stages(args)
+    if args.cusolver:
+        return run_cusolver(args)
     if args.batched:
         return run_batched(args)
     if args.adjoint:
