@@ -715,6 +715,20 @@ def run_stages(args):
     return 0
 
 
+def library_solve(A, B):
+    """All eigenpairs of A x = lambda B x from torch.linalg calls: B = L L^H,
+    A' = L^-1 A L^-H (two triangular solves, Hermitised), A' = Z diag(w) Z^H,
+    X = L^-H Z."""
+    import torch
+    L = torch.linalg.cholesky(B)
+    Y = torch.linalg.solve_triangular(L, A, upper=False)
+    Ap = torch.linalg.solve_triangular(L, Y.conj().transpose(0, 1), upper=False)
+    Ap = 0.5 * (Ap + Ap.conj().transpose(0, 1))
+    w, Z = torch.linalg.eigh(Ap)
+    X = torch.linalg.solve_triangular(L.conj().transpose(0, 1), Z, upper=True)
+    return w, X
+
+
 def run_cusolver(args):
     """Context comparator on the same GPU: the generalized solve assembled from
     library calls (torch.linalg on CUDA: Cholesky, two triangular solves for
@@ -727,16 +741,7 @@ def run_cusolver(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     n = args.n
-
-    def solve(A, B):
-        L = torch.linalg.cholesky(B)
-        Y = torch.linalg.solve_triangular(L, A, upper=False)
-        Ap = torch.linalg.solve_triangular(L, Y.conj().transpose(0, 1), upper=False)
-        Ap = 0.5 * (Ap + Ap.conj().transpose(0, 1))
-        w, Z = torch.linalg.eigh(Ap)
-        X = torch.linalg.solve_triangular(L.conj().transpose(0, 1), Z, upper=True)
-        return w, X
-
+    solve = library_solve
     a, b, _ = inputs.make_pair(512, 0)
     solve(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
     A_np, B_np, lam = inputs.make_pair(n, args.seed, "uniform", -10.0, 10.0, device=dev if n > 3000 else None)

@@ -24,3 +24,21 @@ def test_chase_roofline():
     assert bench.chase_roofline({"ms": 0.0, "bytes": 1.0, "flops": 1.0}, 8000.0, 1.0) is None
     r = bench.chase_roofline({"ms": 1.0, "bytes": 1e6, "flops": 0.0}, None, None)
     assert r["hbm_frac"] is None and r["dfma_frac"] is None
+
+
+def test_library_comparator_algebra():
+    """The context comparator's solve (run on CUDA by --cusolver) is the
+    generalized eigensolution: checked on the CPU at small n."""
+    import numpy as np
+    import torch
+    from paper_1207_1773_gb300 import inputs
+    n = 40
+    A, B, lam = inputs.make_pair(n, 3)
+    At, Bt = torch.from_numpy(A), torch.from_numpy(B)
+    w, X = bench.library_solve(At, Bt)
+    eps = np.finfo(np.float64).eps
+    assert np.max(np.abs(w.numpy() - lam)) <= 10 * n * eps * np.linalg.norm(A, 2) / np.linalg.eigvalsh(B).min()
+    R = At @ X - (Bt @ X) * w[None, :]
+    assert torch.linalg.norm(R).item() <= 100 * n * eps * torch.linalg.norm(At).item() * torch.linalg.norm(X).item()
+    O = X.conj().T @ Bt @ X - torch.eye(n, dtype=torch.complex128)
+    assert torch.linalg.norm(O).item() <= 100 * n * eps
