@@ -41,19 +41,18 @@ def bind(path):
     """Load a compiled oracle library and declare its signatures."""
     lib = ctypes.CDLL(path)
     P, I = ctypes.c_void_p, ctypes.c_int
-    if True:
-        lib.orc_num_threads.restype = I
-        lib.orc_potrf.argtypes = [I, P, I]
-        lib.orc_potrf.restype = I
-        lib.orc_hegst.argtypes = [I, P, I, P, I]
-        lib.orc_hetrd.argtypes = [I, P, I, P, P, P, I, P]
-        lib.orc_steqr.argtypes = [I, P, P, P, I]
-        lib.orc_steqr.restype = I
-        lib.orc_sort_eig.argtypes = [I, P, P, I]
-        lib.orc_unmtr.argtypes = [I, I, P, I, P, P, I]
-        lib.orc_trsm_lh.argtypes = [I, I, P, I, P, I]
-        lib.orc_hegv.argtypes = [I, P, I, P, I, I, I, P, P, I]
-        lib.orc_hegv.restype = I
+    lib.orc_num_threads.restype = I
+    lib.orc_potrf.argtypes = [I, P, I]
+    lib.orc_potrf.restype = I
+    lib.orc_hegst.argtypes = [I, P, I, P, I]
+    lib.orc_hetrd.argtypes = [I, P, I, P, P, P, I, P]
+    lib.orc_steqr.argtypes = [I, P, P, P, I]
+    lib.orc_steqr.restype = I
+    lib.orc_sort_eig.argtypes = [I, P, P, I]
+    lib.orc_unmtr.argtypes = [I, I, P, I, P, P, I]
+    lib.orc_trsm_lh.argtypes = [I, I, P, I, P, I]
+    lib.orc_hegv.argtypes = [I, P, I, P, I, I, I, P, P, I]
+    lib.orc_hegv.restype = I
     return lib
 
 

@@ -339,7 +339,7 @@ struct UCfg {
   static constexpr unsigned BUFC = NC * UBN;         // TMEM columns of one buffer
   static constexpr unsigned COLS = CPLX ? 512 : 256; // allocation (two buffers)
   static constexpr int STB = NC * (U_APL + U_BPL);   // bytes per pipeline stage
-  static constexpr size_t SMEM = (size_t)STAGES * STB + (size_t)NC * UBN * OPITCH + 8 * (STAGES + 2) + 16;
+  static constexpr size_t SMEM = (size_t)STAGES * STB + (size_t)NC * UBN * OPITCH + 8 * (STAGES + 3) + 16;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -413,8 +413,9 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   constexpr int STB = CF::STB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stile = smem_raw + STAGES * STB;
+  // bars: [0, STAGES) stage empty, STAGES + b accumulator b full, STAGES + 2 drain (before TMEM is freed)
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile + NC * UBN * OPITCH);
-  unsigned* tslot = reinterpret_cast<unsigned*>(bars + STAGES + 2);
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + STAGES + 3);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   const size_t planeA = (size_t)M * Kp, planeB = (size_t)N * Kp;
 
   if (t == 0) {
-    for (int i = 0; i < STAGES + 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
+    for (int i = 0; i < STAGES + 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sabort = 0;
   }
@@ -557,9 +558,11 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     const bool unit_start = (kt % KTC) == 0;
     cp_wait<STAGES - 2>();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    // one decision for the whole CTA: a timeout recorded by any thread before
+    // this barrier stops every thread at the same iteration
+    const int stop = __syncthreads_or(*sabort);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (*sabort) { aborted = true; break; }
+    if (stop) { aborted = true; break; }
     if (t == 0) {
       const unsigned dbuf = tmem + (unsigned)(u & 1) * CF::BUFC;
       const unsigned sA = smem_addr(smem_raw + s * STB), sB = sA + NC * U_APL;
@@ -593,6 +596,13 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   }
   if (!aborted) epilogue(mpc * nch - 1);
   cp_wait<0>();
+  // TMEM is freed only after every MMA this CTA issued has completed: the
+  // issuing thread commits once more and waits for that commit (bounded), also
+  // on the path that gave up early
+  if (t == 0) {
+    umma_commit(smem_addr(bars + STAGES + 2));
+    if (!mbar_wait(smem_addr(bars + STAGES + 2), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CF::COLS));
@@ -630,7 +640,7 @@ struct WsCfg {
   static constexpr int NC = UCfg<CPLX>::NC;
   static constexpr int STB = UCfg<CPLX>::STB;
   static constexpr int STILE = NC * UBN * OPITCH;
-  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 2 * (size_t)STILE + 8 * (WS_STAGES + 4) + 16;
+  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 2 * (size_t)STILE + 8 * (WS_STAGES + 5) + 16;
 };
 
 template <bool CPLX>
@@ -644,8 +654,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stile0 = smem_raw + WS_STAGES * STB;
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile0 + 2 * WF::STILE);
-  // bars: [0, S) stage empty, S + b accumulator full, S + 2 + b accumulator drained
-  unsigned* tslot = reinterpret_cast<unsigned*>(bars + WS_STAGES + 4);
+  // bars: [0, S) stage empty, S + b accumulator full, S + 2 + b accumulator drained,
+  // S + 4 drain of every issued MMA (before TMEM is freed)
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + WS_STAGES + 5);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
@@ -676,6 +687,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   if (t == 0) {
     for (int i = 0; i < WS_STAGES + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + WS_STAGES + 4)));
     for (int i = 0; i < 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + WS_STAGES + 2 + i)), "r"(WS_EPI));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -762,6 +774,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
       cp_commit();
     }
     cp_wait<0>();
+    // every MMA issued here has completed before TMEM is freed (bounded wait;
+    // also when a timeout made the other waits give up)
+    if (t == 0) {
+      umma_commit(smem_addr(bars + WS_STAGES + 4));
+      if (!mbar_wait(smem_addr(bars + WS_STAGES + 4), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
+    }
   } else {
     // ---------------- epilogue (256 threads): row 32 q + lane, columns 64 hh .. 64 hh + 63
     const int q = w & 3, hh = (w - 4) >> 2, il = 32 * q + lane, et = t - 128;

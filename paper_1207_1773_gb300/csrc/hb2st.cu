@@ -14,8 +14,16 @@
 // inside the columns that the next sweeps eliminate, so the working band needs
 // 2*nb sub-diagonals.  Step (s, j) overlaps step (s-1, j+1) and nothing later
 // of sweep s-1, so sweep s may run step j once sweep s-1 has finished step
-// j+1: the sweeps are pipelined over persistent CTAs (sweep s on CTA s mod G),
+// j+1: the sweeps are pipelined over persistent CTAs (or CTA clusters),
 // handed over through per-sweep progress counters with bounded waits.
+//
+// Forward progress does not rest on all CTAs being resident at once: a CTA
+// (cluster) takes its next sweep from a global ticket counter when it is
+// ready, so sweeps are handed out in the order in which running CTAs ask for
+// them.  The holder of sweep s-1 took its ticket earlier and is therefore
+// already running; it waits only on sweep s-2, and sweep 0 waits on nothing,
+// so the chain always advances whatever the number of co-resident CTAs (an
+// ordinary launch: no cooperative or co-scheduling guarantee is needed).
 #include <algorithm>
 #include <cooperative_groups.h>
 #include "internal.cuh"
@@ -34,10 +42,14 @@ struct ChaseArgs {
   int ldb, n, nb, J;
   cplx* V2;       // (s*J + j)*nb
   cplx* tau2;     // s*J + j
-  int* progress;  // n counters, PSTRIDE ints apart (one 128-byte line each)
+  int* progress;  // n counters, PSTRIDE ints apart (one 128-byte line each), then the sweep ticket
   int* st;
 };
 constexpr int PSTRIDE = 32;
+
+// The sweep-ticket counter: one line after the n progress counters (zeroed
+// with them before the launch).
+__device__ __forceinline__ int* ticket_ptr(const ChaseArgs& a) { return a.progress + (size_t)a.n * PSTRIDE; }
 
 __device__ __forceinline__ cplx* bat(const ChaseArgs& a, int r, int c) {
   return a.WB + (size_t)(r - c) + (size_t)c * a.ldb;
@@ -65,6 +77,7 @@ struct ChaseSmem {
   cplx tau;
   double beta;
   int ok;
+  int sweep;
 };
 
 // Reflector from x[0..len) (in smem): on return x = v (v[0] = 1), S.tau and
@@ -158,14 +171,20 @@ __device__ void two_sided(ChaseSmem& S, int L, const cplx* v, cplx tau) {
   __syncthreads();
 }
 
-// One CTA per sweep at a time (sweep s on CTA s mod G).  Each step stages its
-// blocks in shared memory: one coalesced read of D (lower, mirrored) and E
-// from the working band, the step's arithmetic on chip, one write back.
+// One CTA per sweep at a time (sweeps taken from the ticket counter).  Each
+// step stages its blocks in shared memory: one coalesced read of D (lower,
+// mirrored) and E from the working band, the step's arithmetic on chip, one
+// write back.
 __global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
   extern __shared__ __align__(16) unsigned char chase_smem_raw[];
   ChaseSmem& S = *reinterpret_cast<ChaseSmem*>(chase_smem_raw);
   const int t = threadIdx.x, n = A.n, nb = A.nb;
-  for (int s = blockIdx.x; s <= n - 2; s += gridDim.x) {
+  for (;;) {
+    if (t == 0) S.sweep = atomicAdd(ticket_ptr(A), 1);
+    __syncthreads();
+    const int s = S.sweep;
+    __syncthreads();  // every thread has read the ticket before thread 0 may take the next
+    if (s > n - 2) return;
     const int ntask = (n - 1 - s + nb - 1) / nb;
     const int ntask_prev = (s > 0) ? (n - 1 - (s - 1) + nb - 1) / nb : 0;
     cplx tprev = mk(0.0, 0.0);
@@ -299,6 +318,7 @@ struct ClSmem {
   cplx tau, scal;
   double beta;
   int ok;
+  int sweep;
 };
 
 __device__ __forceinline__ cplx warp_sum8(cplx v) {  // sum over aligned groups of 8 lanes
@@ -317,14 +337,21 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
   const int rank = (int)cl.block_rank();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int n = A.n, nb = A.nb;
-  const int ncl = gridDim.x / CS, cid = blockIdx.x / CS;
   const int R0 = rank * RS;
   const int row8 = t >> 3, sub = t & 7;  // 8 threads per local row
   ClSmem* peer[CS];
 #pragma unroll
   for (int q = 0; q < CS; ++q) peer[q] = cl.map_shared_rank(&S, q);
 
-  for (int s = cid; s <= n - 2; s += ncl) {
+  for (;;) {
+    // ---- next sweep: rank 0 takes a ticket and publishes it to the cluster
+    if (rank == 0 && t == 0) S.sweep = atomicAdd(ticket_ptr(A), 1);
+    cl.sync();  // #0
+    const int s = peer[0]->sweep;
+    if (s > n - 2) {
+      cl.sync();  // nobody leaves while another CTA may still read its shared memory
+      return;
+    }
     const int ntask = (n - 1 - s + nb - 1) / nb;
     const int ntask_prev = (s > 0) ? (n - 1 - (s - 1) + nb - 1) / nb : 0;
     cplx tprev = mk(0.0, 0.0);
@@ -534,7 +561,8 @@ __global__ void k_band_out(const cplx* WB, int ldb, int n, double* d, double* e)
 }  // namespace
 
 size_t hb2st_ws_bytes(int n, int nb) {
-  return (size_t)(2 * nb + 1) * std::max(n, 1) * sizeof(cplx) + (size_t)std::max(n, 1) * PSTRIDE * sizeof(int) + 512;
+  return (size_t)(2 * nb + 1) * std::max(n, 1) * sizeof(cplx) + (size_t)(std::max(n, 1) + 1) * PSTRIDE * sizeof(int) +
+         512;
 }
 
 int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* e, cplx* V2, cplx* tau2) {
@@ -544,13 +572,13 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
   const size_t save = a.off;
   const int ldb = 2 * nb + 1;
   cplx* WB = a.take<cplx>((size_t)ldb * n);
-  int* prog = a.take<int>((size_t)n * PSTRIDE);
+  int* prog = a.take<int>((size_t)(n + 1) * PSTRIDE);  // progress counters, then the sweep ticket
   if (!a.ok() || !WB) { a.off = save; return GBHE_EWORKSPACE; }
   const int J = hb2st_J(n, nb);
   k_band_in<<<std::min<size_t>(((size_t)ldb * n + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, n, nb, WB, ldb);
   count_launch();
   GBHE_CUDA(cudaGetLastError());
-  GBHE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)n * PSTRIDE, c.st));
+  GBHE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)(n + 1) * PSTRIDE, c.st));
   if (n >= 2) {
     ChaseArgs ca;
     ca.WB = WB; ca.ldb = ldb; ca.n = n; ca.nb = nb; ca.J = J; ca.V2 = V2; ca.tau2 = tau2;
@@ -558,7 +586,7 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     // sweep s starts about 2 steps after sweep s-1 and lasts at most J steps, so
     // at most ceil(J/2) + 1 sweeps are ever active: more CTAs would only wait
     // (and would keep other streams' kernels off their SMs)
-    const int G = std::min(std::min(c.num_sms, n - 1), (J + 1) / 2 + 2);
+    int G = std::min(std::min(c.num_sms, n - 1), (J + 1) / 2 + 2);
     count_launch();
     double fl = 0.0;
     if (prof_on()) {
@@ -574,45 +602,51 @@ int hb2st_run(Ctx& c, int n, int nb, const cplx* A, int lda, double* d, double* 
     }
     const double by = 16.0 * ((double)n * J * nb + 2.0 * ldb * n);
     ProfScope prof(c.st, GBHE_PROF_CHASE, fl, by);
-    // Cluster form (CS CTAs per sweep) when the device accepts a cooperative
-    // cluster launch with every cluster resident; decided once, outside stream
-    // capture, else the one-CTA form.
+    // Cluster form (CS CTAs per sweep) when the device runs cluster launches of
+    // this kernel, else the one-CTA form; decided once per device, outside
+    // stream capture.  Both are ordinary launches: the ticket order, not
+    // co-residency, guarantees progress, so the grid is only capped at the
+    // clusters that fit at once (more would only wait for a free slot).
     static int cl_states[MAX_DEVICES] = {};  // 0 unknown, 1 usable, -1 not usable
+    static int cl_max[MAX_DEVICES] = {};     // clusters resident at once
     const int dev = device_slot();
     if (dev < 0) { a.off = save; return GBHE_ECUDA; }
     int& cl_state = cl_states[dev];
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     GBHE_CUDA(cudaStreamIsCapturing(c.st, &cap));
-    bool launched = false;
-    if (cl_state == 1 || (cl_state == 0 && cap == cudaStreamCaptureStatusNone)) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(G * CS);
-      cfg.blockDim = dim3(CT);
-      cfg.dynamicSmemBytes = sizeof(ClSmem);
-      cfg.stream = c.st;
-      cudaLaunchAttribute at[2];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = CS;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      at[1].id = cudaLaunchAttributeCooperative;
-      at[1].val.cooperative = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 2;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = sizeof(ClSmem);
+    cfg.stream = c.st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cl_state == 0 && cap == cudaStreamCaptureStatusNone) {
+      cfg.gridDim = dim3(CS);
       int maxc = 0;
-      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)k_chase_cl, &cfg) == cudaSuccess && maxc >= G &&
-          cudaLaunchKernelEx(&cfg, k_chase_cl, ca) == cudaSuccess) {
-        launched = true;
+      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)k_chase_cl, &cfg) == cudaSuccess && maxc >= 1) {
         cl_state = 1;
+        cl_max[dev] = maxc;
       } else {
         (void)cudaGetLastError();
-        if (cl_state == 0) cl_state = -1;
+        cl_state = -1;
       }
+    }
+    bool launched = false;
+    if (cl_state == 1) {
+      const int Gc = std::max(1, std::min(G, cl_max[dev]));
+      cfg.gridDim = dim3(Gc * CS);
+      if (cudaLaunchKernelEx(&cfg, k_chase_cl, ca) == cudaSuccess) launched = true;
+      else (void)cudaGetLastError();
     }
     if (!launched) {
       GBHE_CUDA(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChaseSmem)));
-      void* args[] = {&ca};
-      GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_chase, dim3(G), dim3(HT), args, sizeof(ChaseSmem), c.st));
+      k_chase<<<G, HT, sizeof(ChaseSmem), c.st>>>(ca);
+      GBHE_CUDA(cudaGetLastError());
     }
   }
   k_band_out<<<std::min((n + 255) / 256, 1024), 256, 0, c.st>>>(WB, ldb, n, d, e);

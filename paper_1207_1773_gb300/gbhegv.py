@@ -149,6 +149,28 @@ def _block(t, n, m, name):
         raise ValueError("gbhegv: %s must be %d x %d, got %s" % (name, n, m, tuple(t.shape)))
 
 
+def _gemm_dims(opA, opB, A, B, C):
+    """(m, n, k) of C = op(A) op(B) + C with every operand's stored shape
+    checked against them: the C-ABI sees only pointers and leading dimensions,
+    so an operand too small for (opA, opB, m, n, k) would be read past its end."""
+    if opA not in OPS or opB not in ("N", "T", "C"):
+        raise ValueError("gbhegv: operand modes %r, %r" % (opA, opB))
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t.dim() != 2:
+            raise ValueError("gbhegv: %s must be a matrix, got %s" % (name, tuple(t.shape)))
+    m, n = C.shape
+    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    want_a = (m, k) if opA in ("N", "H") else (k, m)
+    want_b = (k, n) if opB == "N" else (n, k)
+    if tuple(A.shape) != want_a or (opA == "H" and m != k):
+        raise ValueError("gbhegv: op%s(A) must be %d x %d for C %d x %d, A is %s"
+                         % (opA, m, k, m, n, tuple(A.shape)))
+    if tuple(B.shape) != want_b:
+        raise ValueError("gbhegv: op%s(B) must be %d x %d for C %d x %d, B is %s"
+                         % (opB, k, n, m, n, tuple(B.shape)))
+    return m, n, k
+
+
 def _want(dtype, device, *ts):
     """Every tensor is a CUDA tensor of `dtype` on `device` (the library reads
     each as that element type on the handle's device)."""
@@ -472,10 +494,9 @@ def set_crt_block(block=16384, device=None):
 
 def zgemm(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     """C = alpha op(A) op(B) + beta C through the library's GEMM engine (in place)."""
-    h = handle(C.device)
     _want(C128, C.device, A, B, C)
-    m, n = C.shape
-    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    m, n, k = _gemm_dims(opA, opB, A, B, C)
+    h = handle(C.device)
     h.ensure_workspace(max(m, n, k), 1, 1)
     a, b = complex(alpha), complex(beta)
     _check("gbhe_zgemm", _load().gbhe_zgemm(h.h, OPS[opA], OPS[opB], m, n, k, _Cplx(a.real, a.imag), _ptr(A),
@@ -489,8 +510,7 @@ def zgemm_static(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     the library's static array (no handle, no workspace), in place.  Calls
     must not overlap in time on one device; m * n <= 2**18."""
     _want(C128, C.device, A, B, C)
-    m, n = C.shape
-    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    m, n, k = _gemm_dims(opA, opB, A, B, C)
     a, b = complex(alpha), complex(beta)
     with torch.cuda.device(C.device):
         _check("gbhe_zgemm_static",
@@ -503,13 +523,12 @@ def zgemm_static(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
 def gemm_crt(opA, opB, A, B, C, alpha=1.0, beta=0.0, lower=False):
     """C = alpha op(A) op(B) + beta C computed exactly-modularly on the FP16
     tensor cores (complex128 or float64 operands), in place."""
-    h = handle(C.device)
     if C.dtype not in (C128, F64):
         raise TypeError("gbhegv: expected complex128 or float64, got %s" % C.dtype)
     _want(C.dtype, C.device, A, B, C)
     cplx = 1 if C.dtype == torch.complex128 else 0
-    m, n = C.shape
-    k = A.shape[1] if opA in ("N", "H") else A.shape[0]
+    m, n, k = _gemm_dims(opA, opB, A, B, C)
+    h = handle(C.device)
     need = ctypes.c_size_t()
     _check("gbhe_crt_workspace_size", _load().gbhe_crt_workspace_size(m, n, k, cplx, ctypes.byref(need)))
     h.ensure_bytes(h.workspace_size(1) + int(need.value) + 4096)
@@ -524,11 +543,18 @@ def hegv_adjoint(w_all, X_all, il, iu, gw, gX, delta):
     """dL/dA and dL/dB (n x n Hermitian, column-major) of the eigenpairs
     il..iu from the whole decomposition (w_all, X_all) and the cotangents
     gw (m) and gX (n x m); see gbhe_hegv_adjoint."""
-    n = X_all.shape[0]
-    m = iu - il + 1
-    h = handle(X_all.device)
     _want(F64, X_all.device, w_all, gw)
     _want(C128, X_all.device, X_all, gX)
+    n = _square(X_all)
+    if not (1 <= il <= iu <= n):
+        raise ValueError("gbhegv: need 1 <= il <= iu <= n = %d, got il=%d iu=%d" % (n, il, iu))
+    m = iu - il + 1
+    if w_all.numel() < n:
+        raise ValueError("gbhegv: w_all holds %d values, needs %d" % (w_all.numel(), n))
+    if gw.numel() < m:
+        raise ValueError("gbhegv: gw holds %d values, needs %d" % (gw.numel(), m))
+    _block(gX, n, m, "gX")
+    h = handle(X_all.device)
     h.ensure_workspace(n, 0, m)
     dA = torch.empty((n, n), dtype=torch.complex128, device=X_all.device).t()
     dB = torch.empty((n, n), dtype=torch.complex128, device=X_all.device).t()

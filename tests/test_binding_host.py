@@ -82,3 +82,63 @@ def test_shapes_are_checked():
         gbhegv._block(torch.zeros((4, 2)), 4, 3, "X")
     with pytest.raises(ValueError):
         gbhegv._block(torch.zeros((5, 3)), 4, 3, "X")
+
+
+def test_gemm_operand_shapes_are_checked():
+    """Operands too small (or too large) for (opA, opB, m, n, k) are refused
+    before any pointer reaches the library (the C-ABI sees only ld)."""
+    z = lambda r, c: torch.zeros((r, c), dtype=torch.complex128)  # noqa: E731
+    assert gbhegv._gemm_dims("N", "N", z(5, 3), z(3, 4), z(5, 4)) == (5, 4, 3)
+    assert gbhegv._gemm_dims("C", "N", z(3, 5), z(3, 4), z(5, 4)) == (5, 4, 3)
+    assert gbhegv._gemm_dims("N", "C", z(5, 3), z(4, 3), z(5, 4)) == (5, 4, 3)
+    assert gbhegv._gemm_dims("H", "T", z(5, 5), z(4, 5), z(5, 4)) == (5, 4, 5)
+    with pytest.raises(ValueError, match="opN\\(A\\)"):
+        gbhegv._gemm_dims("N", "N", z(4, 3), z(3, 4), z(5, 4))   # A has too few rows
+    with pytest.raises(ValueError, match="opN\\(B\\)"):
+        gbhegv._gemm_dims("N", "N", z(5, 3), z(2, 4), z(5, 4))   # B has too few rows
+    with pytest.raises(ValueError, match="opN\\(B\\)"):
+        gbhegv._gemm_dims("N", "N", z(5, 3), z(3, 3), z(5, 4))   # B has too few columns
+    with pytest.raises(ValueError, match="opC\\(B\\)"):
+        gbhegv._gemm_dims("N", "C", z(5, 3), z(3, 3), z(5, 4))
+    with pytest.raises(ValueError, match="opH\\(A\\)"):
+        gbhegv._gemm_dims("H", "N", z(5, 4), z(4, 4), z(5, 4))   # Hermitian A must be square
+    with pytest.raises(ValueError, match="modes"):
+        gbhegv._gemm_dims("X", "N", z(5, 3), z(3, 4), z(5, 4))
+    with pytest.raises(ValueError, match="matrix"):
+        gbhegv._gemm_dims("N", "N", torch.zeros(5, dtype=torch.complex128), z(3, 4), z(5, 4))
+
+
+def test_gemm_entry_points_check_shapes_before_the_library(monkeypatch):
+    """zgemm, zgemm_static and gemm_crt raise on mismatched operands before
+    they touch a handle or the library."""
+    monkeypatch.setattr(gbhegv, "_want", lambda *a, **k: None)
+    monkeypatch.setattr(gbhegv, "handle", lambda *a, **k: pytest.fail("reached the library"))
+    monkeypatch.setattr(gbhegv, "_load", lambda: pytest.fail("reached the library"))
+    A = torch.zeros((4, 3), dtype=torch.complex128)
+    B = torch.zeros((3, 4), dtype=torch.complex128)
+    C = torch.zeros((5, 4), dtype=torch.complex128)
+    for fn in (gbhegv.zgemm, gbhegv.zgemm_static, gbhegv.gemm_crt):
+        with pytest.raises(ValueError, match="opN\\(A\\)"):
+            fn("N", "N", A, B, C)
+
+
+def test_adjoint_argument_lengths_are_checked(monkeypatch):
+    monkeypatch.setattr(gbhegv, "_want", lambda *a, **k: None)
+    monkeypatch.setattr(gbhegv, "handle", lambda *a, **k: pytest.fail("reached the library"))
+    n, m = 6, 3
+    X = torch.zeros((n, n), dtype=torch.complex128)
+    w = torch.zeros(n, dtype=torch.float64)
+    gw = torch.zeros(m, dtype=torch.float64)
+    gX = torch.zeros((n, m), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="w_all"):
+        gbhegv.hegv_adjoint(w[:n - 1], X, 1, m, gw, gX, 0.0)
+    with pytest.raises(ValueError, match="gw"):
+        gbhegv.hegv_adjoint(w, X, 1, m, gw[:m - 1], gX, 0.0)
+    with pytest.raises(ValueError, match="gX"):
+        gbhegv.hegv_adjoint(w, X, 1, m, gw, gX[:, :m - 1], 0.0)
+    with pytest.raises(ValueError, match="gX"):
+        gbhegv.hegv_adjoint(w, X, 1, m, gw, gX[:n - 1], 0.0)
+    with pytest.raises(ValueError, match="il"):
+        gbhegv.hegv_adjoint(w, X, 2, n + 1, gw, gX, 0.0)
+    with pytest.raises(ValueError):
+        gbhegv.hegv_adjoint(w, X[:, :n - 1], 1, m, gw, gX, 0.0)

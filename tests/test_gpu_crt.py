@@ -146,3 +146,37 @@ def test_crt_chunk_boundaries(G, k, cplx):
     G.gemm_crt("N", "N", Ad, Bd, Cd, 1.0, 0.0)
     ref = A @ B
     assert np.all(np.abs(Cd.cpu().numpy() - ref) <= 8 * (k + 2) * EPS * (np.abs(A) @ np.abs(B)))
+
+
+def _exact(a, b):
+    """op(A) op(B) in extended precision (numpy longdouble: 64-bit or more
+    mantissa), so the reference's own rounding is far below the bound tested."""
+    return (a.astype(np.clongdouble) @ b.astype(np.clongdouble))
+
+
+@pytest.mark.parametrize("opA,opB,m,n,k", [("N", "N", 130, 70, 64), ("C", "N", 130, 70, 300),
+                                           ("N", "C", 97, 129, 1031)])
+def test_crt_graded_within_rows_and_columns(G, opA, opB, m, n, k):
+    """Entries graded inside every row of op(A) and column of op(B)
+    (a_ik = g_ik 10^u, u ~ U[-12, 0]).  The engine rounds each row of op(A)
+    (column of op(B)) to 53-bit integers relative to its largest entry, so its
+    error bound is normwise per row and column:
+        |err_ij| <= 4 eps (max_k |a_ik| sum_k |b_kj| + sum_k |a_ik| max_k |b_kj|) + eps |c_ij|,
+    independent of k (the modular products are exact).  This is weaker than an
+    FP64 GEMM's componentwise gamma_k |A||B| for graded rows: the test pins
+    the bound the engine does guarantee."""
+    rng = np.random.default_rng(m + n + k)
+    ra, ca = (m, k) if opA == "N" else (k, m)
+    rb, cb = (k, n) if opB == "N" else (n, k)
+    A = (rng.standard_normal((ra, ca)) + 1j * rng.standard_normal((ra, ca))) * 10.0 ** rng.uniform(-12, 0, (ra, ca))
+    B = (rng.standard_normal((rb, cb)) + 1j * rng.standard_normal((rb, cb))) * 10.0 ** rng.uniform(-12, 0, (rb, cb))
+    a, b = _ops(A, B, opA, opB)
+    Cd = torch.zeros((n, m), dtype=torch.complex128, device=DEV).t()
+    G.gemm_crt(opA, opB, _c(A), _c(B), Cd, 1.0, 0.0)
+    out = Cd.cpu().numpy()
+    ref = _exact(a, b)
+    err = np.abs(out.astype(np.clongdouble) - ref).astype(np.float64)
+    absa, absb = np.abs(a), np.abs(b)
+    bound = 4 * EPS * (absa.max(axis=1)[:, None] * absb.sum(axis=0)[None, :]
+                       + absa.sum(axis=1)[:, None] * absb.max(axis=0)[None, :]) + EPS * np.abs(out)
+    assert np.all(err <= bound), float(np.max(err / bound))
