@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "generalized solve time (s) & GFLOP/s at n=10k complex128 vs one-stage on same GPU"
 UNIT = "GFLOP/s"
 CPU_SAMPLE_N = 2048
+ONESTAGE_REPS = 3
 # Tensor flops of the CRT GEMM per FP64-equivalent flop: 16 moduli, and per
 # complex multiply-add (8 real flops) four real FP16 products of 2 flops each
 # (real operands: one product per real multiply-add) -> 16 x.
@@ -52,6 +53,15 @@ def _load_peaks():
 
 
 PEAKS = _load_peaks()
+
+# DRAM traffic of the product kernels per launch, from one ncu capture of the
+# build it names (dram__bytes_read.sum + dram__bytes_write.sum); None when no
+# capture of the current kernels exists.
+PRODUCT_TRAFFIC = {"bytes_per_launch": None, "source": None}
+
+
+def pm_launches(prof):
+    return prof["crt_mma"]["launches"]
 
 
 def chase_roofline(pc, hbm_gbs, dfma_tflops):
@@ -69,6 +79,33 @@ def chase_roofline(pc, hbm_gbs, dfma_tflops):
 
 def nominal_flops(n, m):
     return 32.0 / 3.0 * n ** 3 + 12.0 * n * n * m
+
+
+def contraction_flops(n, m):
+    """Algorithmic FP64 flops of the stages whose products run on the
+    tensor-core engine, per solve: potrf 4n^3/3, hegst 4n^3, he2hb 16n^3/3,
+    back-transforms Q2 and Q1 8n^2 m each, trsm 4n^2 m (the divide and
+    conquer's merges are not counted: their sizes depend on deflation)."""
+    return 4.0 / 3.0 * n ** 3 + 4.0 * n ** 3 + 16.0 / 3.0 * n ** 3 + 20.0 * n * n * m
+
+
+def tensor_roofline(prof, n, m, steps, peak):
+    """Roofline of the tcgen05 product kernels (k_crt_umma, k_crt_umma_ws):
+    achieved = 16 x the algorithmic FP64 flops (16 moduli; four real FP16
+    products per complex multiply-add) over their summed CUDA-event time;
+    the executed FP64-equivalent flops the engine counted are reported
+    beside it (dense diamond blocks of Q2 execute twice the algorithmic work)."""
+    pm = prof["crt_mma"]
+    if pm["ms"] <= 0:
+        return None
+    sec = pm["ms"] * 1e-3
+    alg = contraction_flops(n, m) * steps
+    ach = CRT_TENSOR_PER_FP64 * alg / sec / 1e12
+    return {"achieved": ach, "frac": (ach / peak) if peak else None,
+            "algorithmic_fp64_flops_per_solve": contraction_flops(n, m),
+            "executed_fp64_flops_per_solve": pm["flops"] / steps,
+            "executed_tensor_tflops": CRT_TENSOR_PER_FP64 * pm["flops"] / sec / 1e12,
+            "product_ms_per_solve": pm["ms"] / steps, "launches_per_solve": pm["launches"] / steps}
 
 
 def parse():
@@ -101,6 +138,12 @@ def parse():
                    help="time each C-ABI stage alone at --n / --frac / --nb (one JSON line)")
     p.add_argument("--cusolver", action="store_true",
                    help="context: the same solve assembled from torch.linalg library calls at --n (one JSON line)")
+    p.add_argument("--frac-study", action="store_true",
+                   help="fraction of the eigenspace: two-stage and one-stage at --n for m/n in {1, 0.25, 0.10}, "
+                        "--steps timed solves each after --warmup (one JSON line)")
+    p.add_argument("--cfg2", action="store_true",
+                   help="the n=20000 clustered, ill-conditioned pair (seed 2): all eigenpairs and the lowest 20%% "
+                        "(accuracy against the constructed spectrum, residual and B-orthonormality, time)")
     return p.parse_args()
 
 
@@ -314,22 +357,24 @@ def run_ours(args):
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        # pinned, column-major (transposed row-major) like the device copies
-        Ah = torch.empty((n, n), dtype=torch.complex128, pin_memory=True).t()
-        Bh = torch.empty((n, n), dtype=torch.complex128, pin_memory=True).t()
-        Ah.copy_(A0)
-        Bh.copy_(B0)
-        Xh = torch.empty((m, n), dtype=torch.complex128).pin_memory().t()
-        wh = torch.empty(m, dtype=torch.float64).pin_memory()
+        # pinned host buffers holding the column-major matrices' storage (the
+        # transposes of row-major tensors), so that every copy is one
+        # contiguous host<->device memcpy
+        Ah = torch.empty((n, n), dtype=torch.complex128, pin_memory=True)
+        Bh = torch.empty((n, n), dtype=torch.complex128, pin_memory=True)
+        Ah.copy_(A0.t())
+        Bh.copy_(B0.t())
+        Xh = torch.empty((m, n), dtype=torch.complex128, pin_memory=True)
+        wh = torch.empty(m, dtype=torch.float64, pin_memory=True)
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            A.copy_(Ah, non_blocking=True)
-            B.copy_(Bh, non_blocking=True)
+            A.t().copy_(Ah, non_blocking=True)
+            B.t().copy_(Bh, non_blocking=True)
             w2, X2 = G.hegv(A, B, 1, m, nb=nb, check=False)
-            Xh.copy_(X2, non_blocking=True)
+            Xh.copy_(X2.t(), non_blocking=True)
             wh.copy_(w2, non_blocking=True)
         f1.record(stream)
         barrier()
@@ -338,20 +383,25 @@ def run_ours(args):
                "h2d_bytes_per_step": int(2 * n * n * 16), "d2h_bytes_per_step": int(n * m * 16 + m * 8),
                "ms_per_step": ms2 / args.steps}
 
-    # ---- one-stage comparator on the same GPU (one untimed warm-up, one timed solve)
+    # ---- one-stage comparator on the same GPU (one untimed warm-up, then
+    # ONESTAGE_REPS solves timed one by one; median and spread)
     onestage = None
     if not args.no_onestage:
         try:
             step(onestage=True)
             barrier()
-            g0 = torch.cuda.Event(enable_timing=True)
-            g1 = torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            w3, _ = step(onestage=True)
-            g1.record(stream)
-            barrier()
-            ms3 = g0.elapsed_time(g1)
-            onestage = {"solve_time_s": ms3 / 1e3, "value": nominal_flops(n, m) / (ms3 * 1e-3) / 1e9,
+            t3 = []
+            for _ in range(ONESTAGE_REPS):
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                w3, _ = step(onestage=True)
+                g1.record(stream)
+                barrier()
+                t3.append(g0.elapsed_time(g1))
+            ms3 = statistics.median(t3)
+            onestage = {"solve_time_s": ms3 / 1e3, "solve_time_s_all": [round(t / 1e3, 4) for t in t3],
+                        "value": nominal_flops(n, m) / (ms3 * 1e-3) / 1e9,
                         "unit": UNIT, "max_abs_eig_err": float(np.max(np.abs(w3.cpu().numpy() - lam[:m]))),
                         "two_stage_speedup": ms3 / (ms / args.steps)}
         except Exception as ex:  # reported, not hidden
@@ -362,18 +412,21 @@ def run_ours(args):
     pd = prof[dom]
     roof = None
     if dom == "crt":
-        # the dominant kernel is the residue-product kernel k_crt_umma
-        # (tcgen05.mma kind::f16): algorithmic tensor flops = 16 x the
-        # FP64-equivalent flops of the products it serves, over its own time
-        pm = prof["crt_mma"]
-        ach = CRT_TENSOR_PER_FP64 * pm["flops"] / (pm["ms"] * 1e-3) / 1e12
-        fp64eq = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
+        # the dominant kernels are the residue products k_crt_umma /
+        # k_crt_umma_ws (tcgen05.mma kind::f16); achieved from the algorithmic
+        # flops of the contractions they serve (see tensor_roofline)
         peak = PEAKS.get("bf16_tflops")
-        roof = {"kernel": "k_crt_umma (tcgen05.mma kind::f16, FP32 accumulators in TMEM)", "bound": "tensor",
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": (ach / peak) if peak else None,
-                "traffic": None,
+        tr = tensor_roofline(prof, n, m, args.steps, peak)
+        fp64eq = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
+        roof = {"kernel": "k_crt_umma / k_crt_umma_ws (tcgen05.mma kind::f16, FP32 accumulators in TMEM)",
+                "bound": "tensor", "achieved": tr["achieved"], "peak": peak, "unit": "TFLOP/s",
+                "frac": tr["frac"], "traffic": PRODUCT_TRAFFIC["bytes_per_launch"],
+                "traffic_source": PRODUCT_TRAFFIC["source"],
                 "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json; fp16 runs at the bf16 rate)",
-                "launches": pm["launches"], "ms": pm["ms"],
+                "launches": pm_launches(prof), "ms": prof["crt_mma"]["ms"],
+                "algorithmic_fp64_flops_per_solve": tr["algorithmic_fp64_flops_per_solve"],
+                "executed_fp64_flops_per_solve": tr["executed_fp64_flops_per_solve"],
+                "executed_tensor_tflops": tr["executed_tensor_tflops"],
                 "crt_gemm_fp64_equivalent_tflops": fp64eq,
                 "crt_gemm_fp64_equivalent_frac_of_fp64_peak": fp64eq / dmma_peak,
                 "crt_gemm_phase_ms": {k: round(prof[k]["ms"], 1) for k in ("crt_prep", "crt_mma", "crt_rec")}}
@@ -733,7 +786,8 @@ def run_cusolver(args):
     """Context comparator on the same GPU: the generalized solve assembled from
     library calls (torch.linalg on CUDA: Cholesky, two triangular solves for
     L^-1 A L^-H, the Hermitian eigensolver, one triangular solve for X), all
-    eigenpairs, on the same seeded pair; one warm-up solve at n = 512 first."""
+    eigenpairs, on the same seeded pair; one warm-up solve at the measured
+    size, then max(--steps, 3) timed solves (median and spread)."""
     import numpy as np
     import torch
 
@@ -742,21 +796,131 @@ def run_cusolver(args):
     torch.cuda.set_device(dev)
     n = args.n
     solve = library_solve
-    a, b, _ = inputs.make_pair(512, 0)
-    solve(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
     A_np, B_np, lam = inputs.make_pair(n, args.seed, "uniform", -10.0, 10.0, device=dev if n > 3000 else None)
     A, B = torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev)
     st = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(st)
-    w, _ = solve(A, B)
-    e1.record(st)
-    torch.cuda.synchronize(dev)
-    t = e0.elapsed_time(e1) / 1e3
+    solve(A, B)
+    times = []
+    for _ in range(max(args.steps, 3)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        w, _ = solve(A, B)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(times)
     print(json.dumps({"comparator": "library pipeline (torch.linalg on CUDA: cholesky, solve_triangular, eigh)",
-                      "n": n, "m": n, "solve_time_s": t, "value": nominal_flops(n, n) / t / 1e9, "unit": UNIT,
+                      "n": n, "m": n, "solve_time_s": t, "solve_time_s_all": [round(x, 4) for x in times],
+                      "value": nominal_flops(n, n) / t / 1e9, "unit": UNIT,
                       "max_abs_eig_err": float(np.max(np.abs(w.cpu().numpy() - lam)))}))
+    return 0
+
+
+def run_frac_study(args):
+    """Fraction-of-eigenspace study on the same GPU and the same pair: for each
+    m/n in {1, 0.25, 0.10}, the two-stage and the one-stage solve, each timed
+    --steps times (CUDA events around the C-ABI call, inputs restored from
+    device copies outside the events) after --warmup untimed solves; median
+    times and the two-stage speed-up."""
+    import numpy as np
+    import torch
+
+    from paper_1207_1773_gb300 import gbhegv as G
+    from paper_1207_1773_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, nb = args.n, args.nb
+    A_np, B_np, lam = inputs.make_pair(n, args.seed, "uniform", -10.0, 10.0, device=dev if n > 3000 else None)
+    A0, B0 = G.colmajor(A_np, dev), G.colmajor(B_np, dev)
+    A, B = torch.empty_like(A0), torch.empty_like(B0)
+    G.handle(dev).ensure_workspace(n, nb, n)
+    st = torch.cuda.current_stream(dev)
+    rows = []
+    for frac in (1.0, 0.25, 0.10):
+        m = inputs.fraction_iu(n, frac)
+        res = {"frac": frac, "m": m}
+        for name, one in (("two_stage", False), ("one_stage", True)):
+            times, w = [], None
+            for it in range(args.warmup + args.steps):
+                A.copy_(A0)
+                B.copy_(B0)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                w, _ = G.hegv(A, B, 1, m, nb=nb, onestage=one, check=False)
+                e1.record(st)
+                torch.cuda.synchronize(dev)
+                if it >= args.warmup:
+                    times.append(e0.elapsed_time(e1) / 1e3)
+            if G.handle(dev).status() != 0:
+                raise RuntimeError("solver status during the fraction study")
+            res[name + "_s"] = statistics.median(times)
+            res[name + "_s_all"] = [round(t, 4) for t in times]
+            res[name + "_max_abs_eig_err"] = float(np.max(np.abs(w.cpu().numpy() - lam[:m])))
+        res["two_stage_speedup"] = res["one_stage_s"] / res["two_stage_s"]
+        rows.append(res)
+    print(json.dumps({"fraction_study": rows, "n": n, "nb": nb, "steps": args.steps, "warmup": args.warmup,
+                      "workload": "n=%d complex128 pair, Lambda~U[-10,10], seed %d" % (n, args.seed)}), flush=True)
+    return 0
+
+
+def run_cfg2(args):
+    """The n = 20000 pair with a clustered spectrum (90 % uniform in [-1, 1],
+    10 % in clusters of 8 spaced 1e-10) and an ill-conditioned B (diag(L)
+    log-uniform in [1, 100]), seed 2: all eigenpairs and the lowest 20 %, one
+    timed solve each after a warm-up solve at n = 2048.  Reports the error
+    against the constructed spectrum with its bound 10 n eps max|Lambda|
+    kappa(B), and the residual and B-orthonormality ratios on 64 sampled
+    eigenvectors (products formed with torch on the device)."""
+    import numpy as np
+    import torch
+
+    from paper_1207_1773_gb300 import gbhegv as G
+    from paper_1207_1773_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    eps = float(np.finfo(np.float64).eps)
+    n, nb = 20000, args.nb
+    a, b, _ = inputs.make_pair(2048, 2, "clustered", -1.0, 1.0, ldiag="loguniform")
+    G.hegv(G.colmajor(a, dev), G.colmajor(b, dev), 1, 2048, nb=nb)
+    t0 = time.time()
+    A_np, B_np, lam = inputs.make_pair(n, 2, "clustered", -1.0, 1.0, ldiag="loguniform", device=dev)
+    A0, B0 = G.colmajor(A_np, dev), G.colmajor(B_np, dev)
+    del A_np, B_np
+    gen_s = time.time() - t0
+    ev = torch.linalg.eigvalsh(B0).cpu().numpy()
+    kappa = float(ev[-1] / ev[0])
+    tol = 10 * n * eps * float(np.max(np.abs(lam))) * kappa
+    st = torch.cuda.current_stream(dev)
+    out = []
+    for frac in (1.0, 0.20):
+        m = inputs.fraction_iu(n, frac)
+        A, B = A0.clone(), B0.clone()
+        G.handle(dev).ensure_workspace(n, nb, m)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        w, X = G.hegv(A, B, 1, m, nb=nb, check=False)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        status = G.handle(dev).status()
+        t = e0.elapsed_time(e1) / 1e3
+        del A, B
+        err = float(np.max(np.abs(w.cpu().numpy() - lam[:m])))
+        cols = torch.from_numpy(np.unique(np.linspace(0, m - 1, 64).astype(int))).to(dev)
+        Xs, ws = X[:, cols], w[cols]
+        res = (torch.linalg.norm(A0 @ Xs - (B0 @ Xs) * ws[None, :])
+               / (n * eps * torch.linalg.norm(A0) * torch.linalg.norm(Xs))).item()
+        orth = (torch.linalg.norm(Xs.conj().t() @ (B0 @ Xs) - torch.eye(len(cols), dtype=torch.complex128, device=dev))
+                / (n * eps)).item()
+        del X
+        out.append({"frac": frac, "m": m, "solve_time_s": t, "gflops": nominal_flops(n, m) / t / 1e9,
+                    "status": status, "max_abs_eig_err": err, "eig_tol": tol, "residual_ratio": res,
+                    "orth_ratio": orth})
+    print(json.dumps({"cfg2": out, "n": n, "nb": nb, "kappa_B": kappa, "gen_s": gen_s,
+                      "workload": "n=20000 complex128 pair, clustered Lambda (10% in clusters of 8 spaced 1e-10), "
+                                  "diag(L) log-uniform in [1,100], seed 2"}), flush=True)
     return 0
 
 
@@ -770,6 +934,10 @@ def main():
         return run_stages(args)
     if args.cusolver:
         return run_cusolver(args)
+    if args.frac_study:
+        return run_frac_study(args)
+    if args.cfg2:
+        return run_cfg2(args)
     if args.batched:
         return run_batched(args)
     if args.adjoint:

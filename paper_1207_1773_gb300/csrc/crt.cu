@@ -872,25 +872,6 @@ __device__ __forceinline__ double int160_to_double(unsigned (&D)[5], int sc) {
   return __longlong_as_double((long long)bits);
 }
 
-// CRT value of residue byte `sh / 8` of every word w[l] (one word per modulus).
-// The tables (W_l, y_l / p_l, M) of the reconstruction, copied to shared memory
-// by each block and read through a volatile pointer at every use, so that the
-// compiler does not keep all of them in registers across the element loop.
-struct CrtTables {
-  unsigned W[NMOD][4];
-  float frac[NMOD];
-  unsigned M[4];
-};
-
-__device__ __forceinline__ const volatile CrtTables* load_tables() {
-  __shared__ CrtTables tb;
-  for (int i = threadIdx.x; i < NMOD * 4; i += blockDim.x) tb.W[i / 4][i % 4] = c_W[i / 4][i % 4];
-  for (int i = threadIdx.x; i < NMOD; i += blockDim.x) tb.frac[i] = c_frac[i];
-  if (threadIdx.x < 4) tb.M[threadIdx.x] = c_M[threadIdx.x];
-  __syncthreads();
-  return &tb;
-}
-
 // 160-bit value of sum_w X_w 2^(32 w) for four 64-bit column sums X_w < 2^63
 __device__ __forceinline__ void combine160(unsigned (&D)[5], unsigned long long X0, unsigned long long X1,
                                            unsigned long long X2, unsigned long long X3) {
@@ -924,59 +905,62 @@ __device__ __forceinline__ double crt_finish(const unsigned long long (&X)[4], f
 
 // Reconstruct four consecutive rows i0..i0+3 of column j of one output tile
 // (tile base `T` in the tile-major residue layout, offset `loc` inside it)
-// and update C.  For every modulus the table words W_l are read once and
-// applied to all eight values (four rows, real and imaginary parts): the
-// CRT sum of each value is kept as four independent 64-bit word sums (each
-// term < 2^40, sixteen terms < 2^44), carries propagated once at the end.
+// and update C.  One component (Re, then Im) at a time: its CRT sums are
+// kept as four independent 64-bit word sums per value (each term < 2^40,
+// sixteen terms < 2^44), carries propagated once at the end.  The loops over
+// the moduli and the words are unrolled, so the table words W_l and y_l / p_l
+// are constant-bank operands of the multiply-adds (no registers, no shared
+// memory), and only one component's sums are live at a time.
+// CRT values of one component (c) of four consecutive rows.
+template <int NCOUT>
+__device__ __noinline__ void crt_component4(const unsigned char* T, int loc, int c, const int (&sc)[4],
+                                            double (&v)[4]) {
+  const unsigned Mw[4] = {c_M[0], c_M[1], c_M[2], c_M[3]};
+  unsigned w[NMOD];
+#pragma unroll
+  for (int l = 0; l < NMOD; ++l) w[l] = __ldcs(reinterpret_cast<const unsigned*>(T + (size_t)(l * NCOUT + c) * OTILE + loc));
+  unsigned long long X[4][4];
+  float F[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    F[r] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) X[r][k] = 0ull;
+  }
+#pragma unroll
+  for (int l = 0; l < NMOD; ++l) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const unsigned cv = (w[l] >> (8 * r)) & 0xFFu;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) X[r][k] += (unsigned long long)cv * c_W[l][k];
+      F[r] = fmaf((float)cv, c_frac[l], F[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) v[r] = crt_finish(X[r], F[r], Mw, sc[r]);
+}
+
 template <bool CPLX>
-__device__ __forceinline__ void crt_store4(const volatile CrtTables* tb, const unsigned char* T, int loc, int i0,
-                                           int j, int M, int lower, const int* ea, int ebj, double2 alpha,
-                                           double2 beta, void* Cv, int ldc) {
+__device__ __forceinline__ void crt_store4(const unsigned char* T, int loc, int i0, int j, int M, int lower,
+                                           const int* ea, int ebj, double2 alpha, double2 beta, void* Cv, int ldc) {
   constexpr int NCOUT = CPLX ? 2 : 1;
   const bool beta0 = (beta.x == 0.0 && beta.y == 0.0);
   const bool beta1 = (beta.x == 1.0 && beta.y == 0.0);
   const bool alpha1 = (alpha.x == 1.0 && alpha.y == 0.0);
   const bool alpham1 = (alpha.x == -1.0 && alpha.y == 0.0);
-  unsigned w[NCOUT][NMOD];
+  int sc[4];
 #pragma unroll
-  for (int l = 0; l < NMOD; ++l)
-#pragma unroll
-    for (int c = 0; c < NCOUT; ++c)
-      w[c][l] = *reinterpret_cast<const unsigned*>(T + (size_t)(l * NCOUT + c) * OTILE + loc);
-  unsigned long long X[NCOUT][4][4];
-  float F[NCOUT][4];
-#pragma unroll
-  for (int c = 0; c < NCOUT; ++c)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      F[c][r] = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) X[c][r][k] = 0ull;
-    }
-#pragma unroll
-  for (int l = 0; l < NMOD; ++l) {
-    const unsigned W0 = tb->W[l][0], W1 = tb->W[l][1], W2 = tb->W[l][2], W3 = tb->W[l][3];
-    const float fr = tb->frac[l];
-#pragma unroll
-    for (int c = 0; c < NCOUT; ++c)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const unsigned cv = (w[c][l] >> (8 * r)) & 0xFFu;
-        X[c][r][0] += (unsigned long long)cv * W0;
-        X[c][r][1] += (unsigned long long)cv * W1;
-        X[c][r][2] += (unsigned long long)cv * W2;
-        X[c][r][3] += (unsigned long long)cv * W3;
-        F[c][r] = fmaf((float)cv, fr, F[c][r]);
-      }
-  }
-  const unsigned Mw[4] = {tb->M[0], tb->M[1], tb->M[2], tb->M[3]};
+  for (int r = 0; r < 4; ++r) sc[r] = (i0 + r < M) ? ea[i0 + r] + ebj - 104 : 0;
+  double v[NCOUT][4];
+  crt_component4<NCOUT>(T, loc, 0, sc, v[0]);
+  if (CPLX) crt_component4<NCOUT>(T, loc, 1, sc, v[NCOUT - 1]);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int i = i0 + r;
     if (i >= M || (lower && i < j)) continue;
-    const int sc = ea[i] + ebj - 104;
-    const double vr = crt_finish(X[0][r], F[0][r], Mw, sc);
-    const double vi = CPLX ? crt_finish(X[NCOUT - 1][r], F[NCOUT - 1][r], Mw, sc) : 0.0;
+    const double vr = v[0][r];
+    const double vi = CPLX ? v[NCOUT - 1][r] : 0.0;
     double2 out;
     if (alpha1) out = make_double2(vr, vi);
     else if (alpham1) out = make_double2(-vr, -vi);
@@ -1001,7 +985,6 @@ __device__ __forceinline__ void crt_store4(const volatile CrtTables* tb, const u
 // consecutive rows of a tile column (4-byte loads of every residue block).
 __global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const int* ea, const int* eb, GemmArgs g,
                                   int cplx) {
-  const volatile CrtTables* tb = load_tables();
   const int TM = (M + CBM - 1) / CBM, TN = (N + CBN - 1) / CBN;
   const int ncout = cplx ? 2 : 1;
   const size_t per_tile = OTILE / 4;
@@ -1015,8 +998,8 @@ __global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const 
     if (i0 >= M || j >= N) continue;
     if (g.lower_only && i0 + 3 < j) continue;
     const unsigned char* T = Out + tile * NMOD * ncout * OTILE;
-    if (cplx) crt_store4<true>(tb, T, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, g.C, g.ldc);
-    else crt_store4<false>(tb, T, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, g.C, g.ldc);
+    if (cplx) crt_store4<true>(T, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, g.C, g.ldc);
+    else crt_store4<false>(T, loc, i0, j, M, g.lower_only, ea, eb[j], g.alpha, g.beta, g.C, g.ldc);
   }
 }
 
@@ -1024,7 +1007,6 @@ __global__ void k_crt_reconstruct(const unsigned char* Out, int M, int N, const 
 // (tiles laid out for maxM x maxN per entry).
 __global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, int nbatch, int maxM, int maxN,
                                    const int* ea, const int* eb, double2 alpha, double2 beta, int cplx) {
-  const volatile CrtTables* tb = load_tables();
   const int TM = (maxM + CBM - 1) / CBM, TN = (maxN + CBN - 1) / CBN;
   const int ncout = cplx ? 2 : 1;
   const size_t per_tile = OTILE / 4;
@@ -1045,10 +1027,10 @@ __global__ void k_bcrt_reconstruct(const unsigned char* Out, const CrtDesc* D, i
                (d.cmap ? (ptrdiff_t)(d.cmap[j] - j) * d.ldc * (ptrdiff_t)(cplx ? sizeof(double2) : sizeof(double)) : 0);
     const unsigned char* T = Out + tile * NMOD * ncout * OTILE;
     if (cplx)
-      crt_store4<true>(tb, T, loc, i0, j, d.M, 0, ea + (size_t)z * maxM, eb[(size_t)z * maxN + j], alpha, beta, Cj,
+      crt_store4<true>(T, loc, i0, j, d.M, 0, ea + (size_t)z * maxM, eb[(size_t)z * maxN + j], alpha, beta, Cj,
                        d.ldc);
     else
-      crt_store4<false>(tb, T, loc, i0, j, d.M, 0, ea + (size_t)z * maxM, eb[(size_t)z * maxN + j], alpha, beta, Cj,
+      crt_store4<false>(T, loc, i0, j, d.M, 0, ea + (size_t)z * maxM, eb[(size_t)z * maxN + j], alpha, beta, Cj,
                         d.ldc);
   }
 }
@@ -1261,7 +1243,11 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
   int* eb = ea + M;
   const Operand oa = make_operand(g.A, g.lda, M, K, g.opA, true, cplx);
   const Operand ob = make_operand(g.B, g.ldb, N, K, g.opB, false, cplx);
-  const double flops = (cplx ? 8.0 : 2.0) * (double)M * N * K;
+  // executed FP64-equivalent flops of this call: lower-only products count the
+  // outputs on and below the diagonal only (the tiles above it are skipped)
+  const double mn = std::min(M, N);
+  const double outs = g.lower_only ? mn * M - mn * (mn - 1.0) / 2.0 : (double)M * N;
+  const double flops = (cplx ? 8.0 : 2.0) * outs * K;
   ProfScope prof(st, GBHE_PROF_CRT, flops, 0.0);
   {
     ProfScope pp(st, GBHE_PROF_CRT_PREP, 0.0, 0.0);

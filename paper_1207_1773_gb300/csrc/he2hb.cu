@@ -8,8 +8,12 @@
 //       rows in shared memory; two bounded grid barriers per column);
 //   (c) two-sided update of the trailing matrix A22 <- Q^H A22 Q as
 //       X = A22 V T,  W = X - 1/2 V (T^H V^H X),  A22 -= V W^H + W V^H
-//       (DMMA GEMMs; A22 read as Hermitian from its lower triangle and only
-//       the lower triangle written).
+//       (A22 read as Hermitian from its lower triangle and only the lower
+//       triangle written).  The rank-2nb update is one product,
+//       A22 -= [V W] [W V]^H, so the trailing matrix is read and written once
+//       per panel with a contraction of 2nb: V, W and a second copy of V sit
+//       side by side in one buffer, [V W] and [W V] are two overlapping
+//       column ranges of it.
 #include <algorithm>
 #include "internal.cuh"
 
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(PT) k_panel_qr(PanelArgs p) {
 size_t he2hb_ws_bytes(int n, int nb, int num_sms) {
   size_t nn = (size_t)std::max(n, 1);
   size_t b = 0;
-  b += nn * nb * sizeof(cplx) * 3 + 3 * 256;          // V, VT, X
+  b += nn * nb * sizeof(cplx) * 4 + 2 * 256;          // [V X V], VT
   b += (size_t)nb * nb * sizeof(cplx) * 2 + 2 * 256;  // Y, Z
   b += (size_t)(num_sms + 1) * (nb + 1) * sizeof(cplx) + 256;
   b += 256 * 2;
@@ -174,14 +178,16 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
   if (n <= 0) return 0;
   Arena& a = c.arena;
   const size_t save = a.off;
-  cplx* V = a.take<cplx>((size_t)n * nb);
+  // VXV: V (explicit, from the panel kernel), then X, then a copy of V, each
+  // kr columns wide with leading dimension n; nb + 2 nb columns are reserved
+  // (the panel kernel writes nb columns of V, zero beyond kr)
+  cplx* VXV = a.take<cplx>((size_t)n * 3 * nb);
   cplx* VT = a.take<cplx>((size_t)n * nb);
-  cplx* X = a.take<cplx>((size_t)n * nb);
   cplx* Ys = a.take<cplx>((size_t)nb * nb);
   cplx* Zs = a.take<cplx>((size_t)nb * nb);
   cplx* part = a.take<cplx>((size_t)(c.num_sms + 1) * (nb + 1));
   cplx* alpha = a.take<cplx>(1);
-  if (!a.ok() || !V) { a.off = save; return GBHE_EWORKSPACE; }
+  if (!a.ok() || !VXV) { a.off = save; return GBHE_EWORKSPACE; }
   GBHE_CUDA(cudaMemsetAsync(tau1, 0, sizeof(cplx) * n, c.st));
   const int npan = (n + nb - 1) / nb;
   GBHE_CUDA(cudaMemsetAsync(T1, 0, sizeof(cplx) * (size_t)npan * nb * nb, c.st));
@@ -189,6 +195,9 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
   for (int k = 0; k + nb < n; k += nb) {
     const int mp = n - k - nb;
     const int kr = std::min(nb, mp);
+    cplx* V = VXV;
+    cplx* X = VXV + (size_t)kr * n;
+    cplx* V2c = VXV + (size_t)2 * kr * n;
     // ---- panel QR
     int G = std::min(c.num_sms, std::max(1, (mp + 7) / 8));
     int chunk = (mp + G - 1) / G;
@@ -223,8 +232,10 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
                     c.gemm_scratch_bytes))) break;
     if ((rc = zgemm(c, gemm_args(OP_C, OP_N, kr, kr, kr, one, T, nb, Ys, nb, zero, Zs, nb), nullptr, 0))) break;
     if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, kr, kr, mk(-0.5, 0), V, n, Zs, nb, one, X, n), nullptr, 0))) break;
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0))) break;
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, kr, mone, X, n, V, n, one, A22, lda, 1), nullptr, 0))) break;
+    // A22 -= [V X] [X V]^H (lower triangle), one contraction of 2 kr
+    GBHE_CUDA(cudaMemcpy2DAsync(V2c, sizeof(cplx) * n, V, sizeof(cplx) * n, sizeof(cplx) * mp, kr,
+                                cudaMemcpyDeviceToDevice, c.st));
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, 2 * kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0))) break;
   }
   a.off = save;
   return rc;

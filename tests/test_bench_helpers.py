@@ -42,3 +42,20 @@ def test_library_comparator_algebra():
     assert torch.linalg.norm(R).item() <= 100 * n * eps * torch.linalg.norm(At).item() * torch.linalg.norm(X).item()
     O = X.conj().T @ Bt @ X - torch.eye(n, dtype=torch.complex128)
     assert torch.linalg.norm(O).item() <= 100 * n * eps
+
+
+def test_contraction_flops_and_tensor_roofline():
+    """The algorithmic FP64 flops of the engine-served stages at n = m = 10000
+    (potrf 4n^3/3 + hegst 4n^3 + he2hb 16n^3/3 + Q2 8n^2m + Q1 8n^2m + trsm 4n^2m
+    = 3.0667e13), and the roofline built from them: 16 x those flops over the
+    product kernels' time, independent of what the engine counted as executed."""
+    import bench
+    n = m = 10000
+    assert abs(bench.contraction_flops(n, m) - (32.0 / 3.0 * n ** 3 + 20.0 * n * n * m)) < 1.0
+    assert abs(bench.contraction_flops(n, m) / 3.0666666666666668e13 - 1.0) < 1e-12
+    prof = {"crt_mma": {"ms": 2 * 3096.0, "flops": 2 * 4.69e13, "launches": 2 * 2978}}
+    tr = bench.tensor_roofline(prof, n, m, 2, 1941.1)
+    assert abs(tr["achieved"] - 16 * 3.0666666666666668e13 / 3.096 / 1e12) < 1e-6
+    assert abs(tr["frac"] - tr["achieved"] / 1941.1) < 1e-12
+    assert abs(tr["executed_fp64_flops_per_solve"] - 4.69e13) < 1.0
+    assert bench.tensor_roofline({"crt_mma": {"ms": 0.0, "flops": 0.0, "launches": 0}}, n, m, 1, 1.0) is None
