@@ -13,7 +13,8 @@
 //
 // Q1 (panel block reflectors of stage 1).  Q1 = Q_0 Q_1 ... with
 // Q_p = I - V_p T_p V_p^H on rows p*nb+nb .. n-1, applied last panel first
-// as three DMMA GEMMs: W = V^H X, W = T W, X -= V W.
+// as three products, formed transposed so that the nb-wide side is the
+// column dimension: Wt = X^H V, Wt = Wt T^H, X -= V Wt^H.
 #include <algorithm>
 #include "internal.cuh"
 
@@ -160,8 +161,11 @@ __global__ void __launch_bounds__(256) k_q2_build(int n, int nb, int J, const cp
 }
 
 // Descriptors of one wavefront step t for the batched products
-//   W_z = V_z^H X[r0 : r0+Wh, c0 : c0+mc]          (GEMM 1)
-//   X[r0 : r0+Wh, c0 : c0+mc] -= U_z W_z            (GEMM 2)
+//   Wt_z = X[r0 : r0+Wh, c0 : c0+mc]^H V_z          (GEMM 1, mc x nb: W_z^H)
+//   X[r0 : r0+Wh, c0 : c0+mc] -= U_z Wt_z^H         (GEMM 2)
+// GEMM 1 is formed transposed so that its long dimension (the columns of X)
+// is the row dimension of the product and its nb-wide side the column
+// dimension, which the product kernel tiles 64 wide without idle MMA rows.
 __global__ void k_q2_desc(int n, int nb, int J, int t, int b_lo, int cnt, const cplx* Vg, const cplx* Ug, cplx* X,
                           int ldx, int c0, int mc, cplx* Wbuf, CrtDesc* D1, CrtDesc* D2) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,16 +173,16 @@ __global__ void k_q2_desc(int n, int nb, int J, int t, int b_lo, int cnt, const 
   const int b = b_lo + z, j = t - 2 * (J - 1 - b);
   const long gid = q2_gid(b, j, J);
   const int r0 = (b + j) * nb + 1, Wh = min(2 * nb - 1, n - r0), W2 = 2 * nb;
-  cplx* Wz = Wbuf + (size_t)z * nb * mc;
+  cplx* Wz = Wbuf + (size_t)z * nb * mc;  // mc x nb, ld mc
   CrtDesc d;
   d.cmap = nullptr;
-  d.A = Vg + (size_t)gid * W2 * nb; d.lda = W2;
-  d.B = X + (size_t)r0 + (size_t)c0 * ldx; d.ldb = ldx;
-  d.C = Wz; d.ldc = nb;
-  d.M = nb; d.N = mc; d.K = Wh;
+  d.A = X + (size_t)r0 + (size_t)c0 * ldx; d.lda = ldx;  // op C: X window^H
+  d.B = Vg + (size_t)gid * W2 * nb; d.ldb = W2;          // op N
+  d.C = Wz; d.ldc = mc;
+  d.M = mc; d.N = nb; d.K = Wh;
   D1[z] = d;
-  d.A = Ug + (size_t)gid * W2 * nb; d.lda = W2;
-  d.B = Wz; d.ldb = nb;
+  d.A = Ug + (size_t)gid * W2 * nb; d.lda = W2;          // op N
+  d.B = Wz; d.ldb = mc;                                   // op C: Wt^H = W
   d.C = X + (size_t)r0 + (size_t)c0 * ldx; d.ldc = ldx;
   d.M = Wh; d.N = mc; d.K = nb;
   D2[z] = d;
@@ -251,7 +255,10 @@ static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const c
   cplx* Ug = ar.take<cplx>((size_t)ng * W2 * nb);
   // column chunk so that one batched product fits the tensor-core workspace
   int mc = std::min(m, 64 * ((m + 63) / 64));
-  while (mc > 64 && crt_batched_ws_bytes(cm, W2, mc, W2, 1) > c.crt_ws_bytes) mc -= 64;
+  auto need = [&](int w) {
+    return std::max(crt_batched_ws_bytes(cm, w, nb, W2, 1), crt_batched_ws_bytes(cm, W2, w, nb, 1));
+  };
+  while (mc > 64 && need(mc) > c.crt_ws_bytes) mc -= 64;
   mc = std::min(mc, m);
   cplx* Wbuf = ar.take<cplx>((size_t)std::max(cm, 1) * nb * mc);
   CrtDesc* D1 = ar.take<CrtDesc>((size_t)std::max(cm, 1));
@@ -286,10 +293,10 @@ static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const c
       if (prof_on())
         for (int z = 0; z < cnt; ++z)
           gfl += 8.0 * nb * mcc * std::min(2 * nb - 1, n - ((b_lo + z + t - 2 * (J - 1 - (b_lo + z))) * nb + 1));
-      rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, nb, mcc, W2 - 1, c.crt_ws,
+      rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, mcc, nb, W2 - 1, c.crt_ws,
                             c.crt_ws_bytes, c.status, gfl);
       if (!rc)
-        rc = crt_gemm_batched(c.st, OP_N, OP_N, mk(-1, 0), mk(1, 0), 1, D2, cnt, W2 - 1, mcc, nb, c.crt_ws,
+        rc = crt_gemm_batched(c.st, OP_N, OP_C, mk(-1, 0), mk(1, 0), 1, D2, cnt, W2 - 1, mcc, nb, c.crt_ws,
                               c.crt_ws_bytes, c.status, gfl);
     }
   }
@@ -303,7 +310,7 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
   Arena& ar = c.arena;
   const size_t save = ar.off;
   cplx* V = ar.take<cplx>((size_t)n * nb);
-  cplx* W1 = ar.take<cplx>((size_t)nb * m);
+  cplx* W1 = ar.take<cplx>((size_t)nb * m);  // m x kr, ld m
   cplx* W2 = ar.take<cplx>((size_t)nb * m);
   if (!ar.ok() || !V) { ar.off = save; return GBHE_EWORKSPACE; }
   const size_t total = (size_t)n * m;
@@ -340,12 +347,12 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
     cplx* Xr = X + (k + nb);
     const cplx* T = T1 + (size_t)p * nb * nb;
     int rc;
-    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, kr, m, mp, one, V, n, Xr, ldx, zero, W1, nb), c.gemm_scratch,
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, m, kr, mp, one, Xr, ldx, V, n, zero, W1, m), c.gemm_scratch,
                     c.gemm_scratch_bytes))) { ar.off = save; return rc; }
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, kr, m, kr, one, T, nb, W1, nb, zero, W2, nb), nullptr, 0))) {
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, m, kr, kr, one, W1, m, T, nb, zero, W2, m), nullptr, 0))) {
       ar.off = save; return rc;
     }
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, m, kr, mone, V, n, W2, nb, one, Xr, ldx), nullptr, 0))) {
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, m, kr, mone, V, n, W2, m, one, Xr, ldx), nullptr, 0))) {
       ar.off = save; return rc;
     }
   }

@@ -320,7 +320,9 @@ constexpr int OPITCH = CBM + 16;  // smem column pitch of the staged tile (bank-
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
 // K-adjacent core matrices 128 B apart, 8-row groups 512 B apart).
 //
-// One CTA computes a UBM x UBN output tile for `mpc` consecutive moduli.  Its
+// One CTA computes a UBM x BN output tile (BN = 128, or 64 for products with
+// at most 64 columns, where a wider tile would leave half of every MMA idle)
+// for `mpc` consecutive moduli.  Its
 // work is a flat sequence of K tiles over those moduli, cut into units (one
 // exact chunk of one modulus).  Each unit accumulates Re and Im (one
 // accumulator for real operands) in one of two TMEM buffers; while the
@@ -329,17 +331,20 @@ constexpr int OPITCH = CBM + 16;  // smem column pitch of the staged tile (bank-
 // layout read by the reconstruction (two CBN-wide tiles per CTA).
 constexpr int UBM = 128, UBN = 128, UBK = 32;
 constexpr int UTHREADS = 256;
-constexpr int U_APL = UBM * UBK * 2, U_BPL = UBN * UBK * 2;  // bytes of one plane tile
-static_assert(UBM == CBM && UBN == 2 * CBN, "a CTA covers two tiles of the residue layout");
-template <bool CPLX>
+constexpr int U_APL = UBM * UBK * 2;  // bytes of one plane tile of op(A)
+static_assert(UBM == CBM && UBN == 2 * CBN, "a wide CTA tile covers two tiles of the residue layout");
+template <bool CPLX, int BN>
 struct UCfg {
+  static_assert(BN == UBN || BN == CBN, "tile width 128 or 64");
   static constexpr int NC = CPLX ? 2 : 1;         // planes per operand = accumulators
   static constexpr int STAGES = CPLX ? 5 : 6;
   static constexpr int KC_TERMS = CPLX ? 256 : 512;  // exact chunk (contraction terms)
-  static constexpr unsigned BUFC = NC * UBN;         // TMEM columns of one buffer
-  static constexpr unsigned COLS = CPLX ? 512 : 256; // allocation (two buffers)
-  static constexpr int STB = NC * (U_APL + U_BPL);   // bytes per pipeline stage
-  static constexpr size_t SMEM = (size_t)STAGES * STB + (size_t)NC * UBN * OPITCH + 8 * (STAGES + 3) + 16;
+  static constexpr int BPL = BN * UBK * 2;           // bytes of one plane tile of op(B)
+  static constexpr unsigned BUFC = NC * BN;          // TMEM columns of one buffer
+  static constexpr unsigned COLS = 2 * BUFC;         // allocation (two buffers; a power of 2 >= 32)
+  static constexpr int NRES = BN / 2;                // columns per epilogue thread
+  static constexpr int STB = NC * (U_APL + BPL);     // bytes per pipeline stage
+  static constexpr size_t SMEM = (size_t)STAGES * STB + (size_t)NC * BN * OPITCH + 8 * (STAGES + 3) + 16;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -394,7 +399,7 @@ __device__ __forceinline__ void tmem_ld16(unsigned addr, float (&v)[16]) {
 }
 
 // grid (TM * TN2 tiles in grouped order, 1, (NMOD/mpc) * nbatch), 256 threads;
-// TM = ceil(maxM/UBM), TN2 = ceil(maxN/UBN).  PA: residue planes of op(A)
+// TM = ceil(maxM/UBM), TN2 = ceil(maxN/BN).  PA: residue planes of op(A)
 // (R = M), PB: of op(B) (R = N); both K-padded to Kp.  Batched form
 // (D != nullptr): blockIdx.z / (NMOD/mpc) is the entry; entry regions of the
 // planes and outputs are sized for maxM / maxN, the layout inside an entry's
@@ -403,22 +408,22 @@ __device__ __forceinline__ void tmem_ld16(unsigned addr, float (&v)[16]) {
 // record GBHE_ETIMEOUT in status[ST_ERR].  Used for products whose moduli span
 // several exact chunks (Kp > KC_TERMS); single-chunk products use
 // k_crt_umma_ws below.
-template <bool CPLX>
+template <bool CPLX, int BN>
 __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, const __half* PB, int M, int N, int Kp,
                                                          unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
                                                          int lower, int mpc, int* status) {
-  using CF = UCfg<CPLX>;
+  using CF = UCfg<CPLX, BN>;
   constexpr int NC = CF::NC;
   constexpr int STAGES = CF::STAGES;
   constexpr int STB = CF::STB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stile = smem_raw + STAGES * STB;
   // bars: [0, STAGES) stage empty, STAGES + b accumulator b full, STAGES + 2 drain (before TMEM is freed)
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile + NC * UBN * OPITCH);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile + NC * BN * OPITCH);
   unsigned* tslot = reinterpret_cast<unsigned*>(bars + STAGES + 3);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
-  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
+  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + BN - 1) / BN;
   const int TN = (maxN + CBN - 1) / CBN;  // tiles of the residue layout
   const int ngrp = NMOD / mpc;
   const int entry = blockIdx.z / ngrp, grp = blockIdx.z % ngrp;
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     PB += (size_t)entry * NMOD * NC * maxN * Kp;
     Out += (size_t)entry * TM * TN * NMOD * NC * OTILE;
   }
-  const int m0 = bx * UBM, n0 = by * UBN;
+  const int m0 = bx * UBM, n0 = by * BN;
   if (m0 >= M || n0 >= N) return;
   if (lower && m0 + UBM - 1 < n0) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   const int nch = (ktiles + KTC - 1) / KTC;
   const int iters = mpc * ktiles;
   // instruction descriptor: f32 accumulator, f16 A and B, both K-major, N, M
-  const unsigned idesc = (1u << 4) | ((unsigned)(UBN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
+  const unsigned idesc = (1u << 4) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
   const unsigned idesc_negA = idesc | (1u << 13);
 
   auto load = [&](int it) {
@@ -482,16 +487,16 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
       cp16(sA + c * U_APL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
     }
 #pragma unroll
-    for (int i = t; i < NC * UBN * 4; i += UTHREADS) {
-      const int c = i / (UBN * 4), rem = i % (UBN * 4), r = rem >> 2, kg = rem & 3;
+    for (int i = t; i < NC * BN * 4; i += UTHREADS) {
+      const int c = i / (BN * 4), rem = i % (BN * 4), r = rem >> 2, kg = rem & 3;
       const bool ok = (n0 + r) < N;
       const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + kg * 8;
-      cp16(sB + c * U_BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
+      cp16(sB + c * CF::BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
     }
   };
 
-  // running residues of this thread's row (32 q + lane) and 64 columns (64 h + x)
-  constexpr int NRES = 64;
+  // running residues of this thread's row (32 q + lane) and NRES columns (NRES h + x)
+  constexpr int NRES = CF::NRES;
   float res[NC][NRES];
 #pragma unroll
   for (int c = 0; c < NC; ++c)
@@ -507,13 +512,13 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int l = l0 + u / nch;
     const float p = (float)c_p[l], pinv = c_pinv[l];
-    const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(64 * h);
+    const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(NRES * h);
     const int il = 32 * q + lane;
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl) {
+    for (int sl = 0; sl < NRES / 16; ++sl) {
       float P[NC][16];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+      for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * BN + sl * 16, P[c]);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int c = 0; c < NC; ++c)
@@ -528,18 +533,18 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
         for (int c = 0; c < NC; ++c) {
           float v = red_sym(res[c][x], p, pinv);
           if (v < 0.f) v += p;  // [0, p)
-          stile[(c * UBN + 64 * h + x) * OPITCH + il] = (unsigned char)(int)v;
+          stile[(c * BN + NRES * h + x) * OPITCH + il] = (unsigned char)(int)v;
           res[c][x] = 0.f;
         }
       }
       __syncthreads();
-      // the two CBN-wide layout tiles of this CTA
-      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
+      // the BN / CBN layout tiles of this CTA
+      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(BN, N - n0);
       for (int i = t; i < NC * ncol * nu; i += UTHREADS) {
         const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, uu = rem % nu;
-        const int tile = (2 * by + jl / CBN) * TM + bx;
+        const int tile = ((BN / CBN) * by + jl / CBN) * TM + bx;
         unsigned char* dst = Out + ((size_t)tile * NMOD + l) * NC * OTILE;
-        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * UBN + jl) * OPITCH + uu * 16);
+        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * BN + jl) * OPITCH + uu * 16);
         *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + (jl % CBN)) * CBM + uu * 16) = v;
       }
     }
@@ -574,10 +579,10 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
         umma_f16(dbuf, ar, br, idesc, first);  // Re (or the real product) += Ar Br
         if constexpr (CPLX) {
           const unsigned long long ai = umma_sdesc(sA + U_APL + kk * 256, 128, 512);
-          const unsigned long long bi = umma_sdesc(sB + U_BPL + kk * 256, 128, 512);
+          const unsigned long long bi = umma_sdesc(sB + CF::BPL + kk * 256, 128, 512);
           umma_f16(dbuf, ai, bi, idesc_negA, 1u);     // Re -= Ai Bi
-          umma_f16(dbuf + UBN, ar, bi, idesc, first);  // Im += Ar Bi
-          umma_f16(dbuf + UBN, ai, br, idesc, 1u);     // Im += Ai Br
+          umma_f16(dbuf + BN, ar, bi, idesc, first);  // Im += Ar Bi
+          umma_f16(dbuf + BN, ai, br, idesc, 1u);     // Im += Ai Br
         }
       }
       umma_commit(smem_addr(bars + s));
@@ -635,20 +640,20 @@ __device__ __forceinline__ void mbar_wait_cta(unsigned bar, unsigned parity, vol
   }
 }
 
-template <bool CPLX>
+template <bool CPLX, int BN>
 struct WsCfg {
-  static constexpr int NC = UCfg<CPLX>::NC;
-  static constexpr int STB = UCfg<CPLX>::STB;
-  static constexpr int STILE = NC * UBN * OPITCH;
+  static constexpr int NC = UCfg<CPLX, BN>::NC;
+  static constexpr int STB = UCfg<CPLX, BN>::STB;
+  static constexpr int STILE = NC * BN * OPITCH;
   static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 2 * (size_t)STILE + 8 * (WS_STAGES + 5) + 16;
 };
 
-template <bool CPLX>
+template <bool CPLX, int BN>
 __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA, const __half* PB, int M, int N,
                                                             int Kp, unsigned char* Out, const CrtDesc* D, int maxM,
                                                             int maxN, int lower, int mpc, int* status) {
-  using CF = UCfg<CPLX>;
-  using WF = WsCfg<CPLX>;
+  using CF = UCfg<CPLX, BN>;
+  using WF = WsCfg<CPLX, BN>;
   constexpr int NC = CF::NC;
   constexpr int STB = CF::STB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -659,7 +664,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   unsigned* tslot = reinterpret_cast<unsigned*>(bars + WS_STAGES + 5);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
-  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
+  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + BN - 1) / BN;
   const int TN = (maxN + CBN - 1) / CBN;
   const int ngrp = NMOD / mpc;
   const int entry = blockIdx.z / ngrp, grp = blockIdx.z % ngrp;
@@ -677,7 +682,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
     PB += (size_t)entry * NMOD * NC * maxN * Kp;
     Out += (size_t)entry * TM * TN * NMOD * NC * OTILE;
   }
-  const int m0 = bx * UBM, n0 = by * UBN;
+  const int m0 = bx * UBM, n0 = by * BN;
   if (m0 >= M || n0 >= N) return;
   if (lower && m0 + UBM - 1 < n0) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -707,7 +712,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
 
   if (w < 4) {
     // ---------------- producers (128 threads); thread 0 also issues the MMAs
-    const unsigned idesc = (1u << 4) | ((unsigned)(UBN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
+    const unsigned idesc = (1u << 4) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
     const unsigned idesc_negA = idesc | (1u << 13);
     auto load = [&](int it) {
       unsigned char* sA = smem_raw + (it % WS_STAGES) * STB;
@@ -723,11 +728,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
         cp16(sA + c * U_APL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
       }
 #pragma unroll
-      for (int i = t; i < NC * UBN * 4; i += 128) {
-        const int c = i / (UBN * 4), rem = i % (UBN * 4), r = rem >> 2, kg = rem & 3;
+      for (int i = t; i < NC * BN * 4; i += 128) {
+        const int c = i / (BN * 4), rem = i % (BN * 4), r = rem >> 2, kg = rem & 3;
         const bool ok = (n0 + r) < N;
         const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + kg * 8;
-        cp16(sB + c * U_BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
+        cp16(sB + c * CF::BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
       }
     };
 #pragma unroll
@@ -756,10 +761,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
           umma_f16(dbuf, ar, br, idesc, first);
           if constexpr (CPLX) {
             const unsigned long long ai = umma_sdesc(sA + U_APL + kk * 256, 128, 512);
-            const unsigned long long bi = umma_sdesc(sB + U_BPL + kk * 256, 128, 512);
+            const unsigned long long bi = umma_sdesc(sB + CF::BPL + kk * 256, 128, 512);
             umma_f16(dbuf, ai, bi, idesc_negA, 1u);
-            umma_f16(dbuf + UBN, ar, bi, idesc, first);
-            umma_f16(dbuf + UBN, ai, br, idesc, 1u);
+            umma_f16(dbuf + BN, ar, bi, idesc, first);
+            umma_f16(dbuf + BN, ai, br, idesc, 1u);
           }
         }
         umma_commit(smem_addr(bars + s));
@@ -781,7 +786,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
       if (!mbar_wait(smem_addr(bars + WS_STAGES + 4), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
     }
   } else {
-    // ---------------- epilogue (256 threads): row 32 q + lane, columns 64 hh .. 64 hh + 63
+    // ---------------- epilogue (256 threads): row 32 q + lane, columns NRES hh .. NRES hh + NRES - 1
+    constexpr int NRES = CF::NRES;
     const int q = w & 3, hh = (w - 4) >> 2, il = 32 * q + lane, et = t - 128;
     for (int li = 0; li < mpc; ++li) {
       const int b = li & 1, l = l0 + li;
@@ -789,12 +795,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
       mbar_wait_cta(smem_addr(bars + WS_STAGES + b), (unsigned)(li >> 1) & 1u, sabort, status);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float p = (float)c_p[l], pinv = c_pinv[l];
-      const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(64 * hh);
+      const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(NRES * hh);
 #pragma unroll 1
-      for (int sl = 0; sl < 4; ++sl) {
+      for (int sl = 0; sl < NRES / 16; ++sl) {
         float P[NC][16];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * UBN + sl * 16, P[c]);
+        for (int c = 0; c < NC; ++c) tmem_ld16(tb + c * BN + sl * 16, P[c]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < NC; ++c)
@@ -802,18 +808,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
           for (int x = 0; x < 16; ++x) {
             float v = red_sym(P[c][x], p, pinv);  // |v| <= p/2 + 1
             if (v < 0.f) v += p;                  // [0, p)
-            stile[(c * UBN + 64 * hh + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
+            stile[(c * BN + NRES * hh + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
           }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_addr(bars + WS_STAGES + 2 + b));  // buffer b may be overwritten
       named_sync(2, WS_EPI);
-      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(UBN, N - n0);
+      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(BN, N - n0);
       for (int i = et; i < NC * ncol * nu; i += WS_EPI) {
         const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, uu = rem % nu;
-        const int tile = (2 * by + jl / CBN) * TM + bx;
+        const int tile = ((BN / CBN) * by + jl / CBN) * TM + bx;
         unsigned char* dst = Out + ((size_t)tile * NMOD + l) * NC * OTILE;
-        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * UBN + jl) * OPITCH + uu * 16);
+        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * BN + jl) * OPITCH + uu * 16);
         *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + (jl % CBN)) * CBM + uu * 16) = v;
       }
     }
@@ -1039,9 +1045,10 @@ inline size_t out_bytes(int M, int N, int cplx) {
   return (size_t)((M + CBM - 1) / CBM) * ((N + CBN - 1) / CBN) * NMOD * (cplx ? 2 : 1) * OTILE;
 }
 
-// Launch of the tcgen05 residue products: moduli per CTA chosen so that the
-// grid covers the GPU at least twice.
-template <bool CPLX, bool ONE>
+// Launch of the tcgen05 residue products: 64-column tiles when every product
+// has at most 64 columns, else 128; moduli per CTA chosen so that the grid
+// covers the GPU at least twice.
+template <bool CPLX, bool ONE, int BN>
 int umma_prepare(int* nsm_out) {
   static bool ready[MAX_DEVICES] = {};
   static int nsm[MAX_DEVICES] = {};
@@ -1049,11 +1056,11 @@ int umma_prepare(int* nsm_out) {
   if (dev < 0) return GBHE_ECUDA;
   if (!ready[dev]) {
     if (ONE)
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma_ws<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)WsCfg<CPLX>::SMEM));
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma_ws<CPLX, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)WsCfg<CPLX, BN>::SMEM));
     else
-      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)UCfg<CPLX>::SMEM));
+      GBHE_CUDA(cudaFuncSetAttribute(k_crt_umma<CPLX, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)UCfg<CPLX, BN>::SMEM));
     GBHE_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
     ready[dev] = true;
   }
@@ -1061,27 +1068,35 @@ int umma_prepare(int* nsm_out) {
   return 0;
 }
 
-template <bool CPLX>
-int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
-                const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
-  const bool one = Kp <= UCfg<CPLX>::KC_TERMS;
+template <bool CPLX, int BN>
+int launch_umma_bn(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
+                   const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
+  const bool one = Kp <= UCfg<CPLX, BN>::KC_TERMS;
   int nsm = 0;
-  int rc = one ? umma_prepare<CPLX, true>(&nsm) : umma_prepare<CPLX, false>(&nsm);
+  int rc = one ? umma_prepare<CPLX, true, BN>(&nsm) : umma_prepare<CPLX, false, BN>(&nsm);
   if (rc) return rc;
-  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + UBN - 1) / UBN;
+  const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + BN - 1) / BN;
   const long tiles = (long)TM * TN2 * nbatch;
   // moduli per CTA: as many as keep at least two CTAs per SM
   int mpc = NMOD;
   while (mpc > 1 && tiles * (NMOD / mpc) < 2L * nsm) mpc /= 2;
   dim3 grid(TM * TN2, 1, (NMOD / mpc) * nbatch);
   if (one)
-    k_crt_umma_ws<CPLX><<<grid, WS_THREADS, WsCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
-                                                                      mpc, status);
+    k_crt_umma_ws<CPLX, BN><<<grid, WS_THREADS, WsCfg<CPLX, BN>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN,
+                                                                             lower, mpc, status);
   else
-    k_crt_umma<CPLX><<<grid, UTHREADS, UCfg<CPLX>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
+    k_crt_umma<CPLX, BN><<<grid, UTHREADS, UCfg<CPLX, BN>::SMEM, st>>>(PA, PB, M, N, Kp, Out, D, maxM, maxN, lower,
                                                                        mpc, status);
   count_launch();
   return 0;
+}
+
+template <bool CPLX>
+int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
+                const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
+  if (maxN <= CBN)
+    return launch_umma_bn<CPLX, CBN>(st, PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, nbatch, status);
+  return launch_umma_bn<CPLX, UBN>(st, PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, nbatch, status);
 }
 
 size_t crt_bytes(int M, int N, int K, int cplx) {

@@ -1,4 +1,6 @@
 """FP64-exact modular GEMM on the FP16 tensor cores, against exact references.
+Shapes cover both product kernels (one exact chunk, several chunks) with both
+tile widths (64 columns when n <= 64, else 128) and ragged edges.
 
 The reference is the product computed in numpy FP64 plus its own error bound;
 the CRT result must agree within the FP64 GEMM error bound
@@ -38,7 +40,8 @@ def _ops(A, B, opA, opB):
 
 
 @pytest.mark.parametrize("opA,opB", [("N", "N"), ("N", "C"), ("C", "N"), ("T", "T"), ("H", "N"), ("N", "T")])
-@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (64, 64, 16), (129, 65, 33), (200, 70, 700), (37, 300, 1500)])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (64, 64, 16), (129, 65, 33), (200, 70, 700), (37, 300, 1500),
+                                   (200, 64, 700), (130, 33, 300)])
 def test_crt_complex(G, opA, opB, m, n, k):
     rng = np.random.default_rng(m + 3 * n + 7 * k)
     if opA == "H":
@@ -58,7 +61,7 @@ def test_crt_complex(G, opA, opB, m, n, k):
     assert np.all(np.abs(out - ref) <= 8 * (k + 2) * EPS * scale)
 
 
-@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (100, 64, 512), (257, 129, 1031)])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (100, 64, 512), (257, 129, 1031), (150, 40, 1500)])
 def test_crt_real(G, m, n, k):
     rng = np.random.default_rng(m * k)
     A = rng.standard_normal((m, k))
