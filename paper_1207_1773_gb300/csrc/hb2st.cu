@@ -42,7 +42,8 @@ struct ChaseArgs {
   int ldb, n, nb, J;
   cplx* V2;       // (s*J + j)*nb
   cplx* tau2;     // s*J + j
-  int* progress;  // n counters, PSTRIDE ints apart (one 128-byte line each), then the sweep ticket
+  int* progress;  // n counters, PSTRIDE ints apart (one 128-byte line each), then the sweep ticket;
+                  // k_chase counts finished steps, k_chase_cl finished (CTA, step) pairs
   int* st;
 };
 constexpr int PSTRIDE = 32;
@@ -296,10 +297,20 @@ __global__ void __launch_bounds__(HT, 1) k_chase(ChaseArgs A) {
 // The same chase with one step split over a cluster of CS CTAs: CTA `rank`
 // owns rows rank*RS .. rank*RS+RS-1 of the step's blocks (D and E).  Every
 // row-local operation (E H_{j-1}, H^H E, D v, the two-sided update) runs on
-// the owning CTA; the three reductions (|x|^2, v^H E, p^H v) and the gathers
-// of x and p go through distributed shared memory, with five cluster barriers
-// per step.  This spreads a step's FP64 arithmetic over CS SMs, which is what
-// bounds the chase: its critical path is ~2n dependent steps.
+// the owning CTA; the data the CTAs exchange go through distributed shared
+// memory with two cluster barriers per step:
+//   A: the rows of x (the column the reflector is made from), the parts of
+//      |x(1:)|^2 and every CTA's verdict on its wait for the previous sweep;
+//   B: the parts of z = v^H E, the rows of p = tau D v and the parts of p^H v
+//      (D v needs only v, so p is formed beside z and both cross one barrier).
+// Every CTA waits for the previous sweep itself and reports its own step
+// through an atomic count (CS per finished step), so no barrier is spent on
+// the hand-over.  A wait that expires is reported at A and the whole cluster
+// returns together (nobody leaves while a peer may still read its shared
+// memory, and nobody is left waiting at a barrier).  The published arrays of
+// A and B are distinct, and a CTA cannot pass barrier A (B) of the next step
+// before every peer has arrived there, i.e. has finished reading this step's
+// data: no data of a step is overwritten while a peer reads it.
 constexpr int CS = 4, CT = 128, RS = MAXNB / CS;
 static_assert(RS * CS == MAXNB && CT % 8 == 0, "row split");
 
@@ -308,11 +319,12 @@ struct ClSmem {
   cplx E[RS * LDS];  // my rows of the sub-diagonal block
   cplx vprev[MAXNB], v[MAXNB], w[MAXNB], z[MAXNB];
   cplx half[2][MAXNB];
-  cplx pub_x[RS];     // published: my rows of x (the column the reflector is made from)
-  cplx pub_z[MAXNB];  // published: my rows' part of v^H E
-  cplx pub_p[RS];     // published: my rows of p = tau D v
-  double pub_nrm;     // published: my rows' part of |x(1:)|^2
-  cplx pub_pv;        // published: my rows' part of p^H v
+  cplx pub_x[RS];     // A: my rows of x
+  double pub_nrm;     // A: my rows' part of |x(1:)|^2
+  int pub_ok;         // A: my wait for the previous sweep succeeded
+  cplx pub_z[MAXNB];  // B: my rows' part of v^H E
+  cplx pub_p[RS];     // B: my rows of p = tau D v
+  cplx pub_pv;        // B: my rows' part of p^H v
   double red[CT / 32];
   cplx redc[CT / 32];
   cplx tau, scal;
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
   for (;;) {
     // ---- next sweep: rank 0 takes a ticket and publishes it to the cluster
     if (rank == 0 && t == 0) S.sweep = atomicAdd(ticket_ptr(A), 1);
-    cl.sync();  // #0
+    cl.sync();
     const int s = peer[0]->sweep;
     if (s > n - 2) {
       cl.sync();  // nobody leaves while another CTA may still read its shared memory
@@ -357,11 +369,11 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
     cplx tprev = mk(0.0, 0.0);
     int Lprev = 0;
     for (int j = 0; j < ntask; ++j) {
-      // ---- wait (rank 0) for sweep s-1 to finish step j+1, then release the cluster
-      if (rank == 0 && t == 0) {
+      // ---- wait (every CTA) for all CS CTAs of sweep s-1 to finish step j+1
+      if (t == 0) {
         int ok = 1;
         if (s > 0) {
-          const int need = min(j + 2, ntask_prev);
+          const int need = CS * min(j + 2, ntask_prev);
           const unsigned long long t0 = gtimer();
           unsigned pause = 16, polls = 0;
           while (ld_acquire_i(&A.progress[(size_t)(s - 1) * PSTRIDE]) < need) {
@@ -376,31 +388,29 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
         }
         S.ok = ok;
       }
-      cl.sync();  // #1
-      if (!peer[0]->ok) {
-        cl.sync();  // nobody leaves while another CTA may still read its shared memory
-        return;
-      }
+      __syncthreads();
       const int a0 = s + 1 + j * nb;
       const int L = min(nb, n - a0);
       const int c0 = a0 - nb;
       const int R1 = min(L, R0 + RS), nloc = max(0, R1 - R0);
-      // ---- stage my rows of D (lower read, mirrored) and of E
-      for (int idx = t; idx < RS * MAXNB; idx += CT) {
-        const int r = idx % RS, c = idx / RS, i = R0 + r;  // consecutive threads: consecutive rows
-        if (r < nloc && c < L && c <= i) {
-          cplx d = __ldcg(bat(A, a0 + i, a0 + c));
-          if (c == i) d.y = 0.0;
-          S.D[r * LDS + c] = d;
+      // ---- stage my rows of D (lower read, mirrored) and of E (only after a wait that succeeded)
+      if (S.ok) {
+        for (int idx = t; idx < RS * MAXNB; idx += CT) {
+          const int r = idx % RS, c = idx / RS, i = R0 + r;  // consecutive threads: consecutive rows
+          if (r < nloc && c < L && c <= i) {
+            cplx d = __ldcg(bat(A, a0 + i, a0 + c));
+            if (c == i) d.y = 0.0;
+            S.D[r * LDS + c] = d;
+          }
+          if (j > 0 && r < nloc && c < Lprev) S.E[r * LDS + c] = __ldcg(bat(A, a0 + i, c0 + c));
         }
-        if (j > 0 && r < nloc && c < Lprev) S.E[r * LDS + c] = __ldcg(bat(A, a0 + i, c0 + c));
+        for (int idx = t; idx < RS * MAXNB; idx += CT) {
+          const int r = idx / MAXNB, c = idx % MAXNB, i = R0 + r;  // consecutive threads: consecutive columns
+          if (r < nloc && c < L && c > i) S.D[r * LDS + c] = cconj(__ldcg(bat(A, a0 + c, a0 + i)));
+        }
+        if (j == 0)
+          for (int r = t; r < nloc; r += CT) S.E[r * LDS] = __ldcg(bat(A, a0 + R0 + r, s));  // x in column 0
       }
-      for (int idx = t; idx < RS * MAXNB; idx += CT) {
-        const int r = idx / MAXNB, c = idx % MAXNB, i = R0 + r;  // consecutive threads: consecutive columns
-        if (r < nloc && c < L && c > i) S.D[r * LDS + c] = cconj(__ldcg(bat(A, a0 + c, a0 + i)));
-      }
-      if (j == 0)
-        for (int r = t; r < nloc; r += CT) S.E[r * LDS] = __ldcg(bat(A, a0 + R0 + r, s));  // x in column 0
       __syncthreads();
       // ---- E <- E H_{j-1}:  y = tau_prev E vprev;  E -= y vprev^H   (row-local)
       if (j > 0) {  // j is uniform: every lane reaches the shuffle of warp_sum8
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
           for (int c = sub; c < Lprev; c += 8) S.E[row8 * LDS + c] = csub(S.E[row8 * LDS + c], cmulc(y, S.vprev[c]));
       }
       __syncthreads();
-      // ---- publish x (my rows of column 0) and my part of |x(1:)|^2
+      // ---- publish x (my rows of column 0), my part of |x(1:)|^2 and my wait's verdict
       double nrm = 0.0;
       for (int r = t; r < nloc; r += CT) {
         const cplx x = S.E[r * LDS];
@@ -427,8 +437,18 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
         double sum = 0.0;
         for (int q = 0; q < CT / 32; ++q) sum += S.red[q];
         S.pub_nrm = sum;
+        S.pub_ok = S.ok;
       }
-      cl.sync();  // #2
+      cl.sync();  // A
+      {
+        int all_ok = 1;
+#pragma unroll
+        for (int q = 0; q < CS; ++q) all_ok &= peer[q]->pub_ok;
+        if (!all_ok) {  // the same verdict in every CTA: the cluster returns together
+          cl.sync();
+          return;
+        }
+      }
       // ---- reflector, identical in every CTA: gather x, then scale
       if (t < L) S.v[t] = peer[t / RS]->pub_x[t % RS];
       if (t == 0) {
@@ -451,26 +471,50 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
       if (t == 0) S.v[0] = mk(1.0, 0.0);
       for (int r = t; r < nloc; r += CT) S.E[r * LDS] = (R0 + r == 0) ? mk(S.beta, 0.0) : mk(0.0, 0.0);
       __syncthreads();
+      // ---- my parts of z = conj(tau) v^H E[:, 1:] (j > 0) and of p = tau D v, p^H v
+      if (j > 0) {
+        const int c = t % MAXNB, h = t / MAXNB;
+        cplx acc = mk(0.0, 0.0);
+        if (c >= 1 && c < Lprev)
+          for (int r = h; r < nloc; r += 2) ccfma(acc, S.v[R0 + r], S.E[r * LDS + c]);
+        S.half[h][c] = acc;
+      }
+      {
+        const bool mine = row8 < nloc;
+        cplx acc = mk(0.0, 0.0);
+        if (mine)
+          for (int c = sub; c < L; c += 8) cfma(acc, S.D[row8 * LDS + c], S.v[c]);
+        const cplx pr = cmul(tau, warp_sum8(acc));  // every lane reaches the shuffle
+        if (mine && sub == 0) S.pub_p[row8] = pr;
+        // my part of p^H v: one contribution per row (the sub == 0 lane)
+        cplx pv = (mine && sub == 0) ? cmulc(S.v[R0 + row8], pr) : mk(0.0, 0.0);  // v conj(p) = conj(p) v
+        pv = warp_sum(pv);
+        if (lane == 0) S.redc[warp] = pv;
+      }
+      __syncthreads();
+      if (j > 0 && t < MAXNB) S.pub_z[t] = cadd(S.half[0][t], S.half[1][t]);
+      if (t == 0) {
+        cplx sum = mk(0.0, 0.0);
+        for (int q = 0; q < CT / 32; ++q) sum = cadd(sum, S.redc[q]);
+        S.pub_pv = sum;
+      }
+      cl.sync();  // B
+      // ---- totals: z (j > 0) and w = p + alpha v, alpha = -1/2 tau p^H v (every thread sums the parts)
+      if (j > 0 && t >= 1 && t < Lprev) {
+        cplx zz = mk(0.0, 0.0);
+        for (int q = 0; q < CS; ++q) zz = cadd(zz, peer[q]->pub_z[t]);
+        S.z[t] = cmul(cconj(tau), zz);
+      }
+      if (t < L) {
+        cplx pvt = mk(0.0, 0.0);
+        for (int q = 0; q < CS; ++q) pvt = cadd(pvt, peer[q]->pub_pv);
+        const cplx al = cscal(-0.5, cmul(tau, pvt));
+        S.w[t] = cadd(peer[t / RS]->pub_p[t % RS], cmul(al, S.v[t]));
+      }
+      __syncthreads();
       if (j == 0) {
         for (int r = t; r < nloc; r += CT) __stcg(bat(A, a0 + R0 + r, s), S.E[r * LDS]);
       } else {
-        // ---- z = conj(tau) v^H E[:, 1:]: my rows' part, published, summed in rank order
-        {
-          const int c = t % MAXNB, h = t / MAXNB;
-          cplx acc = mk(0.0, 0.0);
-          if (c >= 1 && c < Lprev)
-            for (int r = h; r < nloc; r += 2) ccfma(acc, S.v[R0 + r], S.E[r * LDS + c]);
-          S.half[h][c] = acc;
-        }
-        __syncthreads();
-        if (t < MAXNB) S.pub_z[t] = cadd(S.half[0][t], S.half[1][t]);
-        cl.sync();  // #3
-        if (t >= 1 && t < Lprev) {
-          cplx zz = mk(0.0, 0.0);
-          for (int q = 0; q < CS; ++q) zz = cadd(zz, peer[q]->pub_z[t]);
-          S.z[t] = cmul(cconj(tau), zz);
-        }
-        __syncthreads();
         // E[:, c] -= v z_c (c >= 1), then write my rows of E back
         for (int idx = t; idx < RS * MAXNB; idx += CT) {
           const int r = idx % RS, c = idx / RS;
@@ -487,35 +531,7 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
         for (int i = t; i < nb; i += CT) vout[i] = (i < L) ? S.v[i] : mk(0.0, 0.0);
         if (t == 0) A.tau2[(size_t)s * A.J + j] = tau;
       }
-      // ---- two-sided update: p = tau D v (my rows), alpha = -1/2 tau p^H v, w = p + alpha v
-      {
-        const bool mine = row8 < nloc;
-        cplx acc = mk(0.0, 0.0);
-        if (mine)
-          for (int c = sub; c < L; c += 8) cfma(acc, S.D[row8 * LDS + c], S.v[c]);
-        const cplx pr = cmul(tau, warp_sum8(acc));  // every lane reaches the shuffle
-        if (mine && sub == 0) S.pub_p[row8] = pr;
-        // my part of p^H v: one contribution per row (the sub == 0 lane)
-        cplx pv = (row8 < nloc && sub == 0) ? cmulc(S.v[R0 + row8], pr) : mk(0.0, 0.0);  // v conj(p) = conj(p) v
-        pv = warp_sum(pv);
-        if (lane == 0) S.redc[warp] = pv;
-        __syncthreads();
-        if (t == 0) {
-          cplx sum = mk(0.0, 0.0);
-          for (int q = 0; q < CT / 32; ++q) sum = cadd(sum, S.redc[q]);
-          S.pub_pv = sum;
-        }
-      }
-      cl.sync();  // #4
-      if (t == 0) {
-        cplx pvt = mk(0.0, 0.0);
-        for (int q = 0; q < CS; ++q) pvt = cadd(pvt, peer[q]->pub_pv);
-        S.scal = cscal(-0.5, cmul(tau, pvt));
-      }
-      __syncthreads();
-      if (t < L) S.w[t] = cadd(peer[t / RS]->pub_p[t % RS], cmul(S.scal, S.v[t]));
-      __syncthreads();
-      // D -= v w^H + w v^H on my rows; write back the lower part
+      // ---- D -= v w^H + w v^H on my rows; write back the lower part
       for (int idx = t; idx < RS * MAXNB; idx += CT) {
         const int r = idx % RS, c = idx / RS, i = R0 + r;
         if (r < nloc && c < L && c <= i) {
@@ -529,10 +545,10 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
       tprev = tau;
       Lprev = L;
       __syncthreads();
-      cl.sync();  // #5: every CTA's writes (and reads of the published data) done
-      if (rank == 0 && t == 0) {
+      // ---- report my part of the step (every store of this CTA is done)
+      if (t == 0) {
         __threadfence();
-        st_release_i(&A.progress[(size_t)s * PSTRIDE], j + 1);
+        atomicAdd(&A.progress[(size_t)s * PSTRIDE], 1);
       }
     }
   }
