@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(QT) k_apply_q2(int n, int nb, int m, int J, co
 __host__ __device__ inline long q2_gid(int b, int j, int J) { return (long)b * J - (long)b * (b - 1) / 2 + j; }
 
 __global__ void __launch_bounds__(256) k_q2_build(int n, int nb, int J, const cplx* V2, const cplx* tau2, cplx* Vg,
-                                                  cplx* Ug) {
+                                                  cplx* Ug, cplx* Tg) {
   extern __shared__ cplx sm[];
   cplx* T = sm;            // nb x nb
   cplx* G = sm + nb * nb;  // nb x nb (Gram V^H V)
@@ -158,33 +158,123 @@ __global__ void __launch_bounds__(256) k_q2_build(int n, int nb, int J, const cp
     for (int k = max(0, i - nb + 1); k <= min(c, i); ++k) cfma(acc, V[i + (size_t)k * W2], T[k + c * nb]);
     U[q] = acc;
   }
+  cplx* Tout = Tg + (size_t)gid * nb * nb;
+  for (int q = t; q < nb * nb; q += blockDim.x) Tout[q] = T[q];
 }
 
-// Descriptors of one wavefront step t for the batched products
-//   Wt_z = X[r0 : r0+Wh, c0 : c0+mc]^H V_z          (GEMM 1, mc x nb: W_z^H)
+// ---------------------------------------------------------------- merged blocks
+// The diamonds of sweep groups 2c and 2c+1 at the same step j cover rows
+// r0 .. r0+3nb-2 (r0 = (2c + j) nb + 1; the second one starts nb rows lower)
+// and are applied as one block reflector of 2nb columns,
+//   D(2c, j) D(2c+1, j) = I - [V1 V2] [[T1, T12], [0, T2]] [V1 V2]^H,
+//   T12 = -T1 (V1^H V2) T2,   U = V T = [U1, V1 T12 + U2],
+// the group 2c+1 diamond acting first (later sweeps first).  Merged blocks
+// (c, j), j < J - 2c, are numbered mid = c J - c (c - 1) + j and applied in
+// wavefront order w = (C - 1 - c) + j, C = ceil(J / 2): blocks of one step
+// touch disjoint rows, and every block comes after the blocks it overlaps
+// that the sequential order puts first ((c+1, j-2 .. j) and (c, j-1)).  This
+// halves the number of wavefront steps (about 1.5 J instead of 3 J) and
+// doubles the contraction of both products.
+__host__ __device__ inline long q2m_mid(int c, int j, int J) { return (long)c * J - (long)c * (c - 1) + j; }
+inline int q2_pairs(int J) { return (J + 1) / 2; }
+inline long q2m_count(int J) {
+  const int C = q2_pairs(J);
+  return (long)C * J - (long)C * (C - 1);
+}
+
+__global__ void __launch_bounds__(256) k_q2_merge(int n, int nb, int J, const cplx* Vg, const cplx* Ug,
+                                                  const cplx* Tg, cplx* Vm, cplx* Um) {
+  extern __shared__ cplx sm[];
+  cplx* X1 = sm;            // nb x nb: V1^H V2, then T12
+  cplx* X2 = sm + nb * nb;  // nb x nb: V1^H V2 T2
+  const long mid = blockIdx.x;
+  const int C = (J + 1) / 2;
+  int c = 0;
+  while (c + 1 < C && q2m_mid(c + 1, 0, J) <= mid) ++c;
+  const int j = (int)(mid - q2m_mid(c, 0, J));
+  const int b = 2 * c, b2 = b + 1;
+  const bool has2 = b2 < J && j < J - b2;
+  const int W2 = 2 * nb, W3 = 3 * nb;
+  const long g1 = q2_gid(b, j, J), g2 = has2 ? q2_gid(b2, j, J) : 0;
+  const cplx* V1 = Vg + (size_t)g1 * W2 * nb;  // W2 x nb, ld W2
+  const cplx* U1 = Ug + (size_t)g1 * W2 * nb;
+  const cplx* T1 = Tg + (size_t)g1 * nb * nb;  // upper triangular, ld nb
+  const cplx* V2b = Vg + (size_t)g2 * W2 * nb;
+  const cplx* U2 = Ug + (size_t)g2 * W2 * nb;
+  const cplx* T2 = Tg + (size_t)g2 * nb * nb;
+  cplx* V = Vm + (size_t)mid * W3 * W2;  // W3 x 2nb, ld W3
+  cplx* U = Um + (size_t)mid * W3 * W2;
+  const int t = threadIdx.x;
+  // V = [V1 on rows 0..2nb-1 | V2 on rows nb..3nb-1],  U(:, 0:nb) = U1 on rows 0..2nb-1
+  for (int q = t; q < W3 * nb; q += blockDim.x) {
+    const int i = q % W3, k = q / W3;
+    V[i + (size_t)k * W3] = (i < W2) ? V1[i + (size_t)k * W2] : mk(0.0, 0.0);
+    U[i + (size_t)k * W3] = (i < W2) ? U1[i + (size_t)k * W2] : mk(0.0, 0.0);
+    V[i + (size_t)(nb + k) * W3] = (has2 && i >= nb) ? V2b[(i - nb) + (size_t)k * W2] : mk(0.0, 0.0);
+  }
+  if (!has2) {
+    for (int q = t; q < W3 * nb; q += blockDim.x) U[(q % W3) + (size_t)(nb + q / W3) * W3] = mk(0.0, 0.0);
+    return;
+  }
+  // X1 = V1^H V2 (the overlap: rows nb..2nb-1 of V1, rows 0..nb-1 of V2)
+  for (int e = t; e < nb * nb; e += blockDim.x) {
+    const int r = e % nb, k = e / nb;
+    cplx acc = mk(0.0, 0.0);
+    for (int i = 0; i < nb; ++i) ccfma(acc, V1[(nb + i) + (size_t)r * W2], V2b[i + (size_t)k * W2]);
+    X1[r + k * nb] = acc;
+  }
+  __syncthreads();
+  // X2 = X1 T2
+  for (int e = t; e < nb * nb; e += blockDim.x) {
+    const int r = e % nb, k = e / nb;
+    cplx acc = mk(0.0, 0.0);
+    for (int q = 0; q <= k; ++q) cfma(acc, X1[r + q * nb], T2[q + (size_t)k * nb]);
+    X2[r + k * nb] = acc;
+  }
+  __syncthreads();
+  // X1 = T12 = -T1 X2
+  for (int e = t; e < nb * nb; e += blockDim.x) {
+    const int r = e % nb, k = e / nb;
+    cplx acc = mk(0.0, 0.0);
+    for (int q = r; q < nb; ++q) cfma(acc, T1[r + (size_t)q * nb], X2[q + k * nb]);
+    X1[r + k * nb] = cscal(-1.0, acc);
+  }
+  __syncthreads();
+  // U(:, nb:2nb) = V1 T12 on rows 0..2nb-1, plus U2 on rows nb..3nb-1
+  for (int q = t; q < W3 * nb; q += blockDim.x) {
+    const int i = q % W3, k = q / W3;
+    cplx acc = (i >= nb) ? U2[(i - nb) + (size_t)k * W2] : mk(0.0, 0.0);
+    if (i < W2)
+      for (int r = 0; r < nb; ++r) cfma(acc, V1[i + (size_t)r * W2], X1[r + k * nb]);
+    U[i + (size_t)(nb + k) * W3] = acc;
+  }
+}
+
+// Descriptors of merged wavefront step w for the batched products
+//   Wt_z = X[r0 : r0+Wh, c0 : c0+mc]^H V_z          (GEMM 1, mc x 2nb: W_z^H)
 //   X[r0 : r0+Wh, c0 : c0+mc] -= U_z Wt_z^H         (GEMM 2)
 // GEMM 1 is formed transposed so that its long dimension (the columns of X)
-// is the row dimension of the product and its nb-wide side the column
-// dimension, which the product kernel tiles 64 wide without idle MMA rows.
-__global__ void k_q2_desc(int n, int nb, int J, int t, int b_lo, int cnt, const cplx* Vg, const cplx* Ug, cplx* X,
+// is the row dimension of the product.
+__global__ void k_q2_desc(int n, int nb, int J, int w, int c_lo, int cnt, const cplx* Vm, const cplx* Um, cplx* X,
                           int ldx, int c0, int mc, cplx* Wbuf, CrtDesc* D1, CrtDesc* D2) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= cnt) return;
-  const int b = b_lo + z, j = t - 2 * (J - 1 - b);
-  const long gid = q2_gid(b, j, J);
-  const int r0 = (b + j) * nb + 1, Wh = min(2 * nb - 1, n - r0), W2 = 2 * nb;
-  cplx* Wz = Wbuf + (size_t)z * nb * mc;  // mc x nb, ld mc
+  const int C = (J + 1) / 2;
+  const int c = c_lo + z, j = w - (C - 1 - c);
+  const long mid = q2m_mid(c, j, J);
+  const int r0 = (2 * c + j) * nb + 1, Wh = min(3 * nb - 1, n - r0), W3 = 3 * nb, NB2 = 2 * nb;
+  cplx* Wz = Wbuf + (size_t)z * NB2 * mc;  // mc x 2nb, ld mc
   CrtDesc d;
   d.cmap = nullptr;
   d.A = X + (size_t)r0 + (size_t)c0 * ldx; d.lda = ldx;  // op C: X window^H
-  d.B = Vg + (size_t)gid * W2 * nb; d.ldb = W2;          // op N
+  d.B = Vm + (size_t)mid * W3 * NB2; d.ldb = W3;         // op N
   d.C = Wz; d.ldc = mc;
-  d.M = mc; d.N = nb; d.K = Wh;
+  d.M = mc; d.N = NB2; d.K = Wh;
   D1[z] = d;
-  d.A = Ug + (size_t)gid * W2 * nb; d.lda = W2;          // op N
+  d.A = Um + (size_t)mid * W3 * NB2; d.lda = W3;         // op N
   d.B = Wz; d.ldb = mc;                                   // op C: Wt^H = W
   d.C = X + (size_t)r0 + (size_t)c0 * ldx; d.ldc = ldx;
-  d.M = Wh; d.N = mc; d.K = nb;
+  d.M = Wh; d.N = mc; d.K = NB2;
   D2[z] = d;
 }
 
@@ -208,15 +298,25 @@ __global__ void k_panel_v(const cplx* A, int lda, int k, int nb, int mp, int kr,
 
 namespace {
 
-// Largest number of diamonds in one wavefront step.
+// Merged blocks of wavefront step w: pairs c_lo .. c_lo + cnt - 1.
+void q2_step_range(int J, int w, int* c_lo, int* cnt) {
+  const int C = q2_pairs(J);
+  *c_lo = -1;
+  *cnt = 0;
+  for (int c = std::max(0, C - 1 - w); c < C; ++c) {
+    const int j = w - (C - 1 - c);
+    if (j < 0 || j >= J - 2 * c) break;
+    if (*c_lo < 0) *c_lo = c;
+    ++*cnt;
+  }
+}
+
+// Largest number of merged blocks in one wavefront step.
 int q2_max_step(int J) {
   int best = 0;
-  for (int t = 0; t <= 3 * J - 3; ++t) {
-    int cnt = 0;
-    for (int b = 0; b < J; ++b) {
-      const int j = t - 2 * (J - 1 - b);
-      if (j >= 0 && j < J - b) ++cnt;
-    }
+  for (int w = 0; w <= q2_pairs(J) + J - 2; ++w) {
+    int lo, cnt;
+    q2_step_range(J, w, &lo, &cnt);
     best = std::max(best, cnt);
   }
   return best;
@@ -229,9 +329,10 @@ bool q2_use_blocks(const Ctx& c, int n, int nb) {
 size_t q2_block_bytes(int n, int nb, int m) {
   const int J = hb2st_J(n, nb);
   const size_t ng = (size_t)J * (J + 1) / 2;
+  const size_t nm = (size_t)q2m_count(J);
   const size_t cm = (size_t)q2_max_step(J) + 1;
-  return 2 * ng * 2 * nb * nb * sizeof(cplx) + cm * nb * (size_t)std::max(m, 1) * sizeof(cplx) +
-         2 * cm * sizeof(CrtDesc) + 4 * 256;
+  return 2 * ng * 2 * nb * nb * sizeof(cplx) + ng * nb * nb * sizeof(cplx) + 2 * nm * 6 * nb * nb * sizeof(cplx) +
+         cm * 2 * nb * (size_t)std::max(m, 1) * sizeof(cplx) + 2 * cm * sizeof(CrtDesc) + 8 * 256;
 }
 
 }  // namespace
@@ -243,60 +344,65 @@ size_t unmtr_ws_bytes(int n, int nb, int m) {
   return b;
 }
 
-// Q2 applied as wavefront-batched block reflectors on the tensor-core GEMM.
+// Q2 applied as wavefront-batched merged block reflectors on the tensor-core GEMM.
 static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const cplx* tau2, cplx* X, int ldx) {
   Arena& ar = c.arena;
   const size_t save = ar.off;
   const int J = hb2st_J(n, nb);
   const long ng = (long)J * (J + 1) / 2;
+  const long nm = q2m_count(J);
+  const int C = q2_pairs(J);
   const int cm = q2_max_step(J);
-  const int W2 = 2 * nb;
+  const int W2 = 2 * nb, W3 = 3 * nb;
   cplx* Vg = ar.take<cplx>((size_t)ng * W2 * nb);
   cplx* Ug = ar.take<cplx>((size_t)ng * W2 * nb);
+  cplx* Tg = ar.take<cplx>((size_t)ng * nb * nb);
+  cplx* Vm = ar.take<cplx>((size_t)nm * W3 * W2);
+  cplx* Um = ar.take<cplx>((size_t)nm * W3 * W2);
   // column chunk so that one batched product fits the tensor-core workspace
   int mc = std::min(m, 64 * ((m + 63) / 64));
   auto need = [&](int w) {
-    return std::max(crt_batched_ws_bytes(cm, w, nb, W2, 1), crt_batched_ws_bytes(cm, W2, w, nb, 1));
+    return std::max(crt_batched_ws_bytes(cm, w, W2, W3 - 1, 1), crt_batched_ws_bytes(cm, W3 - 1, w, W2, 1));
   };
   while (mc > 64 && need(mc) > c.crt_ws_bytes) mc -= 64;
   mc = std::min(mc, m);
-  cplx* Wbuf = ar.take<cplx>((size_t)std::max(cm, 1) * nb * mc);
+  cplx* Wbuf = ar.take<cplx>((size_t)std::max(cm, 1) * W2 * mc);
   CrtDesc* D1 = ar.take<CrtDesc>((size_t)std::max(cm, 1));
   CrtDesc* D2 = ar.take<CrtDesc>((size_t)std::max(cm, 1));
   if (!ar.ok() || !D2) { ar.off = save; return GBHE_EWORKSPACE; }
   const size_t smem = (size_t)2 * nb * nb * sizeof(cplx);
   GBHE_CUDA(cudaFuncSetAttribute(k_q2_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GBHE_CUDA(cudaFuncSetAttribute(k_q2_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   double fl = 0.0;
   if (prof_on())
     for (int s = 0; s <= n - 2; ++s)
       for (int a0 = s + 1; a0 < n; a0 += nb) fl += 16.0 * std::min(nb, n - a0) * (double)m;
   ProfScope prof(c.st, GBHE_PROF_Q2, fl, 16.0 * ((double)n * J * nb + 2.0 * (double)n * m));
-  k_q2_build<<<(unsigned)ng, 256, smem, c.st>>>(n, nb, J, V2, tau2, Vg, Ug);
+  k_q2_build<<<(unsigned)ng, 256, smem, c.st>>>(n, nb, J, V2, tau2, Vg, Ug, Tg);
+  count_launch();
+  GBHE_CUDA(cudaGetLastError());
+  k_q2_merge<<<(unsigned)nm, 256, smem, c.st>>>(n, nb, J, Vg, Ug, Tg, Vm, Um);
   count_launch();
   GBHE_CUDA(cudaGetLastError());
   int rc = 0;
   for (int c0 = 0; c0 < m && !rc; c0 += mc) {
     const int mcc = std::min(mc, m - c0);
-    for (int t = 0; t <= 3 * J - 3 && !rc; ++t) {
-      int b_lo = -1, cnt = 0;
-      for (int b = 0; b < J; ++b) {
-        const int j = t - 2 * (J - 1 - b);
-        if (j >= 0 && j < J - b) {
-          if (b_lo < 0) b_lo = b;
-          ++cnt;
-        }
-      }
+    for (int w = 0; w <= C + J - 2 && !rc; ++w) {
+      int c_lo, cnt;
+      q2_step_range(J, w, &c_lo, &cnt);
       if (cnt == 0) continue;
-      k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, t, b_lo, cnt, Vg, Ug, X, ldx, c0, mcc, Wbuf, D1, D2);
+      k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, w, c_lo, cnt, Vm, Um, X, ldx, c0, mcc, Wbuf, D1, D2);
       count_launch();
-      double gfl = 0.0;  // each of the two products: 8 nb mcc Wh per diamond
+      double gfl = 0.0;  // each of the two products: 8 (2 nb) mcc Wh per merged block
       if (prof_on())
-        for (int z = 0; z < cnt; ++z)
-          gfl += 8.0 * nb * mcc * std::min(2 * nb - 1, n - ((b_lo + z + t - 2 * (J - 1 - (b_lo + z))) * nb + 1));
-      rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, mcc, nb, W2 - 1, c.crt_ws,
+        for (int z = 0; z < cnt; ++z) {
+          const int cc = c_lo + z, j = w - (C - 1 - cc);
+          gfl += 8.0 * W2 * mcc * std::min(W3 - 1, n - ((2 * cc + j) * nb + 1));
+        }
+      rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, mcc, W2, W3 - 1, c.crt_ws,
                             c.crt_ws_bytes, c.status, gfl);
       if (!rc)
-        rc = crt_gemm_batched(c.st, OP_N, OP_C, mk(-1, 0), mk(1, 0), 1, D2, cnt, W2 - 1, mcc, nb, c.crt_ws,
+        rc = crt_gemm_batched(c.st, OP_N, OP_C, mk(-1, 0), mk(1, 0), 1, D2, cnt, W3 - 1, mcc, W2, c.crt_ws,
                               c.crt_ws_bytes, c.status, gfl);
     }
   }

@@ -393,23 +393,44 @@ __global__ void __launch_bounds__(CT) k_chase_cl(ChaseArgs A) {
       const int L = min(nb, n - a0);
       const int c0 = a0 - nb;
       const int R1 = min(L, R0 + RS), nloc = max(0, R1 - R0);
-      // ---- stage my rows of D (lower read, mirrored) and of E (only after a wait that succeeded)
+      // ---- stage my rows of D (lower read, mirrored) and of E (only after a wait that succeeded):
+      // every load of a thread is issued before the first shared-memory store,
+      // so the step pays one round trip to L2 instead of one per element group
       if (S.ok) {
-        for (int idx = t; idx < RS * MAXNB; idx += CT) {
+        constexpr int PER = RS * MAXNB / CT;
+        cplx dv[PER], ev[PER], uv[PER], xv = mk(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int idx = t + k * CT;
           const int r = idx % RS, c = idx / RS, i = R0 + r;  // consecutive threads: consecutive rows
+          dv[k] = (r < nloc && c < L && c <= i) ? __ldcg(bat(A, a0 + i, a0 + c)) : mk(0.0, 0.0);
+          ev[k] = (j > 0 && r < nloc && c < Lprev) ? __ldcg(bat(A, a0 + i, c0 + c)) : mk(0.0, 0.0);
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int idx = t + k * CT;
+          const int r = idx / MAXNB, c = idx % MAXNB, i = R0 + r;  // consecutive threads: consecutive columns
+          uv[k] = (r < nloc && c < L && c > i) ? __ldcg(bat(A, a0 + c, a0 + i)) : mk(0.0, 0.0);
+        }
+        if (j == 0 && t < nloc) xv = __ldcg(bat(A, a0 + R0 + t, s));  // x in column 0
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int idx = t + k * CT;
+          const int r = idx % RS, c = idx / RS, i = R0 + r;
           if (r < nloc && c < L && c <= i) {
-            cplx d = __ldcg(bat(A, a0 + i, a0 + c));
+            cplx d = dv[k];
             if (c == i) d.y = 0.0;
             S.D[r * LDS + c] = d;
           }
-          if (j > 0 && r < nloc && c < Lprev) S.E[r * LDS + c] = __ldcg(bat(A, a0 + i, c0 + c));
+          if (j > 0 && r < nloc && c < Lprev) S.E[r * LDS + c] = ev[k];
         }
-        for (int idx = t; idx < RS * MAXNB; idx += CT) {
-          const int r = idx / MAXNB, c = idx % MAXNB, i = R0 + r;  // consecutive threads: consecutive columns
-          if (r < nloc && c < L && c > i) S.D[r * LDS + c] = cconj(__ldcg(bat(A, a0 + c, a0 + i)));
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int idx = t + k * CT;
+          const int r = idx / MAXNB, c = idx % MAXNB, i = R0 + r;
+          if (r < nloc && c < L && c > i) S.D[r * LDS + c] = cconj(uv[k]);
         }
-        if (j == 0)
-          for (int r = t; r < nloc; r += CT) S.E[r * LDS] = __ldcg(bat(A, a0 + R0 + r, s));  // x in column 0
+        if (j == 0 && t < nloc) S.E[t * LDS] = xv;
       }
       __syncthreads();
       // ---- E <- E H_{j-1}:  y = tau_prev E vprev;  E -= y vprev^H   (row-local)
