@@ -107,6 +107,9 @@ int make_ctx(gbhe_handle h, int n, void* stream, Ctx* c) {
   if (!c->arena.ok() || !c->gemm_scratch) return GBHE_EWORKSPACE;
   c->engine = h->engine;
   c->crt_block = h->crt_block;
+  c->aux = h->aux;
+  c->ev_a = h->ev_a;
+  c->ev_b = h->ev_b;
   c->crt_ws = nullptr;
   c->crt_ws_bytes = 0;
   if (h->engine == GBHE_ENGINE_CRT) {
@@ -225,8 +228,13 @@ int gbhe_create(gbhe_handle* handle, int device) {
   h->engine = GBHE_ENGINE_CRT;
   h->crt_block = CRT_BLOCK;
   h->nbr_count = 0;
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) prio_hi = 0;
   if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
     cudaFree(h->status); cudaFreeHost(h->status_host); delete h; return GBHE_ECUDA;
   }
   *handle = h;
@@ -236,8 +244,12 @@ int gbhe_create(gbhe_handle* handle, int device) {
 int gbhe_destroy(gbhe_handle h) {
   if (!h) return 0;
   cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->aux);
+  cudaStreamDestroy(h->aux);
   cudaEventDestroy(h->ev_fork);
   cudaEventDestroy(h->ev_join);
+  cudaEventDestroy(h->ev_a);
+  cudaEventDestroy(h->ev_b);
   cudaFree(h->status);
   cudaFreeHost(h->status_host);
   delete h;

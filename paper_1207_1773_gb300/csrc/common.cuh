@@ -146,6 +146,9 @@ struct gbhe_ctx {
   int crt_block;        // largest tensor-core GEMM block (workspace vs speed)
   cudaEvent_t ev_fork;  // fork / join events of gbhe_hegv_batched
   cudaEvent_t ev_join;
+  cudaStream_t aux;     // stage 1's panel stream (lookahead), high priority
+  cudaEvent_t ev_a;     // main -> aux: the next panel's columns are updated
+  cudaEvent_t ev_b;     // aux -> main: the panel is factored
   int nbr_count;        // band-width rule (gbhe_set_nb_rule); 0 = default
   int nbr_n[GBHE_NB_RULE_MAX];
   double nbr_f[GBHE_NB_RULE_MAX];

@@ -1206,7 +1206,7 @@ int gemm(Ctx& c, const GemmArgs& g, int cplx) {
         GemmArgs s = g;
         s.m = mm; s.n = nn; s.k = kk;
         s.lower_only = (g.lower_only && i0 < j0 + nn) ? 1 : 0;
-        if (s.lower_only && (i0 != j0 || mm != nn)) return GBHE_EWORKSPACE;  // blocks are aligned squares
+        if (s.lower_only && i0 != j0) return GBHE_EWORKSPACE;  // the block's corner lies on the diagonal
         if (k0 > 0) s.beta = mk(1.0, 0.0);
         // operand sub-blocks
         const char* A = reinterpret_cast<const char*>(g.A);

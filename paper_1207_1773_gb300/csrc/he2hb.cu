@@ -14,6 +14,12 @@
 //       per panel with a contraction of 2nb: V, W and a second copy of V sit
 //       side by side in one buffer, [V W] and [W V] are two overlapping
 //       column ranges of it.
+// Lookahead (the panel/update overlap of the paper's Figure 1): the update
+// first brings the next panel's nb columns up to date, then the next panel is
+// factored on the handle's panel stream while the rest of the trailing matrix
+// is updated on the caller's stream; the two meet again before the next
+// update.  Panels alternate between two [V X V] buffers so that the next
+// panel never overwrites the V that the running update still reads.
 #include <algorithm>
 #include "internal.cuh"
 
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(PT) k_panel_qr(PanelArgs p) {
 size_t he2hb_ws_bytes(int n, int nb, int num_sms) {
   size_t nn = (size_t)std::max(n, 1);
   size_t b = 0;
-  b += nn * nb * sizeof(cplx) * 4 + 2 * 256;          // [V X V], VT
+  b += nn * nb * sizeof(cplx) * 7 + 3 * 256;          // two [V X V], VT
   b += (size_t)nb * nb * sizeof(cplx) * 2 + 2 * 256;  // Y, Z
   b += (size_t)(num_sms + 1) * (nb + 1) * sizeof(cplx) + 256;
   b += 256 * 2;
@@ -181,50 +187,67 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
   // VXV: V (explicit, from the panel kernel), then X, then a copy of V, each
   // kr columns wide with leading dimension n; nb + 2 nb columns are reserved
   // (the panel kernel writes nb columns of V, zero beyond kr)
-  cplx* VXV = a.take<cplx>((size_t)n * 3 * nb);
+  cplx* VXVb[2];
+  VXVb[0] = a.take<cplx>((size_t)n * 3 * nb);
+  VXVb[1] = a.take<cplx>((size_t)n * 3 * nb);
   cplx* VT = a.take<cplx>((size_t)n * nb);
   cplx* Ys = a.take<cplx>((size_t)nb * nb);
   cplx* Zs = a.take<cplx>((size_t)nb * nb);
   cplx* part = a.take<cplx>((size_t)(c.num_sms + 1) * (nb + 1));
   cplx* alpha = a.take<cplx>(1);
-  if (!a.ok() || !VXV) { a.off = save; return GBHE_EWORKSPACE; }
+  if (!a.ok() || !VXVb[1]) { a.off = save; return GBHE_EWORKSPACE; }
   GBHE_CUDA(cudaMemsetAsync(tau1, 0, sizeof(cplx) * n, c.st));
   const int npan = (n + nb - 1) / nb;
   GBHE_CUDA(cudaMemsetAsync(T1, 0, sizeof(cplx) * (size_t)npan * nb * nb, c.st));
   int rc = 0;
-  for (int k = 0; k + nb < n; k += nb) {
-    const int mp = n - k - nb;
-    const int kr = std::min(nb, mp);
-    cplx* V = VXV;
-    cplx* X = VXV + (size_t)kr * n;
-    cplx* V2c = VXV + (size_t)2 * kr * n;
-    // ---- panel QR
-    int G = std::min(c.num_sms, std::max(1, (mp + 7) / 8));
-    int chunk = (mp + G - 1) / G;
-    size_t smem = (size_t)chunk * nb * sizeof(cplx);
-    if (smem > 200 * 1024) { a.off = save; return -3; }
-    static size_t attr_set[MAX_DEVICES] = {};
-    const int dev = device_slot();
-    if (dev < 0) { a.off = save; return GBHE_ECUDA; }
+  static size_t attr_set[MAX_DEVICES] = {};
+  const int dev = device_slot();
+  if (dev < 0) { a.off = save; return GBHE_ECUDA; }
+  bool pending = false;  // a panel recorded on ev_b that the caller's stream has not joined yet
+  // QR of panel k (columns k .. k+nb-1, rows k+nb .. n-1) on the panel
+  // stream, after the work already queued on the caller's stream, into the
+  // [V X V] buffer `buf`; the caller's stream waits for it before the update.
+  auto panel = [&](int k, cplx* buf) -> int {
+    const int mp = n - k - nb, kr = std::min(nb, mp);
+    const int G = std::min(c.num_sms, std::max(1, (mp + 7) / 8));
+    const int chunk = (mp + G - 1) / G;
+    const size_t smem = (size_t)chunk * nb * sizeof(cplx);
+    if (smem > 200 * 1024) return -3;
     if (smem > 48 * 1024 && smem > attr_set[dev]) {
       GBHE_CUDA(cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
       attr_set[dev] = 210 * 1024;
     }
     PanelArgs pa;
     pa.A = A; pa.lda = lda; pa.n = n; pa.k = k; pa.nb = nb; pa.kr = kr; pa.mp = mp; pa.chunk = chunk;
-    pa.V = V; pa.ldv = n; pa.tau = tau1 + k + 0; pa.T = T1 + (size_t)(k / nb) * nb * nb;
+    pa.V = buf; pa.ldv = n; pa.tau = tau1 + k; pa.T = T1 + (size_t)(k / nb) * nb * nb;
     pa.part = part; pa.alpha = alpha; pa.bar = reinterpret_cast<unsigned*>(c.status + ST_BAR);
     pa.st = c.status;
     void* args[] = {&pa};
+    GBHE_CUDA(cudaEventRecord(c.ev_a, c.st));
+    GBHE_CUDA(cudaStreamWaitEvent(c.aux, c.ev_a, 0));
     count_launch();
     {
       const double fl = 4.0 * (2.0 * mp * (double)kr * kr - 2.0 * (double)kr * kr * kr / 3.0);
-      ProfScope prof(c.st, GBHE_PROF_PANEL, fl, 2.0 * 16.0 * mp * nb);
-      GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PT), args, smem, c.st));
+      ProfScope prof(c.aux, GBHE_PROF_PANEL, fl, 2.0 * 16.0 * mp * nb);
+      GBHE_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PT), args, smem, c.aux));
     }
+    GBHE_CUDA(cudaEventRecord(c.ev_b, c.aux));
+    pending = true;
+    return 0;
+  };
+  if (nb < n && (rc = panel(0, VXVb[0]))) { a.off = save; return rc; }
+  for (int k = 0, p = 0; k + nb < n; k += nb, ++p) {
+    const int mp = n - k - nb;
+    const int kr = std::min(nb, mp);
+    cplx* VXV = VXVb[p & 1];
+    cplx* V = VXV;
+    cplx* X = VXV + (size_t)kr * n;
+    cplx* V2c = VXV + (size_t)2 * kr * n;
+    GBHE_CUDA(cudaStreamWaitEvent(c.st, c.ev_b, 0));  // panel k factored
+    pending = false;
     // ---- trailing update
     cplx* A22 = A + (size_t)(k + nb) + (size_t)(k + nb) * lda;
-    const cplx* T = pa.T;
+    const cplx* T = T1 + (size_t)(k / nb) * nb * nb;
     const cplx one = mk(1, 0), zero = mk(0, 0), mone = mk(-1, 0);
     if ((rc = zgemm(c, gemm_args(OP_N, OP_N, mp, kr, kr, one, V, n, T, nb, zero, VT, n), nullptr, 0))) break;
     if ((rc = zgemm(c, gemm_args(OP_H, OP_N, mp, kr, mp, one, A22, lda, VT, n, zero, X, n), nullptr, 0))) break;
@@ -235,8 +258,22 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
     // A22 -= [V X] [X V]^H (lower triangle), one contraction of 2 kr
     GBHE_CUDA(cudaMemcpy2DAsync(V2c, sizeof(cplx) * n, V, sizeof(cplx) * n, sizeof(cplx) * mp, kr,
                                 cudaMemcpyDeviceToDevice, c.st));
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, 2 * kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0))) break;
+    if (k + 2 * nb < n) {
+      // the next panel's nb columns first, then its QR on the panel stream
+      // beside the update of the remaining columns
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, nb, 2 * kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0)))
+        break;
+      if ((rc = panel(k + nb, VXVb[(p + 1) & 1]))) break;
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp - nb, mp - nb, 2 * kr, mone, V + nb, n, X + nb, n, one,
+                                   A22 + nb + (size_t)nb * lda, lda, 1), nullptr, 0)))
+        break;
+    } else {
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, mp, 2 * kr, mone, V, n, X, n, one, A22, lda, 1), nullptr, 0)))
+        break;
+    }
   }
+  // the caller's stream joins every panel it started (also on an early return)
+  if (pending) cudaStreamWaitEvent(c.st, c.ev_b, 0);
   a.off = save;
   return rc;
 }

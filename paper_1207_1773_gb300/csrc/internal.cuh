@@ -44,6 +44,8 @@ struct Ctx {
   size_t crt_ws_bytes;
   int engine;                 // GBHE_ENGINE_DMMA or GBHE_ENGINE_CRT
   int crt_block;              // largest block of the tensor-core GEMM
+  cudaStream_t aux;           // the handle's panel stream and its two events (stage 1 lookahead)
+  cudaEvent_t ev_a, ev_b;
   Arena arena;                // the rest, for stage temporaries
 };
 
