@@ -12,9 +12,12 @@
 // (2nb-1)-row window of the current (group, j) in shared memory.
 //
 // Q1 (panel block reflectors of stage 1).  Q1 = Q_0 Q_1 ... with
-// Q_p = I - V_p T_p V_p^H on rows p*nb+nb .. n-1, applied last panel first
-// as three products, formed transposed so that the nb-wide side is the
-// column dimension: Wt = X^H V, Wt = Wt T^H, X -= V Wt^H.
+// Q_p = I - V_p T_p V_p^H on rows p*nb+nb .. n-1, applied last panel first,
+// two panels at a time: Q_{p-1} Q_p = I - [V_{p-1} V_p] Tm [V_{p-1} V_p]^H with
+// Tm = [[T_{p-1}, -T_{p-1} (V_{p-1}^H V_p) T_p], [0, T_p]] (V_p starts nb rows
+// lower), as three products formed transposed so that the 2nb-wide side is
+// the column dimension: Wt = X^H V, Wt = Wt Tm^H, X -= V Wt^H.  Pairing halves
+// the passes over X and doubles the contraction of the last product.
 #include <algorithm>
 #include "internal.cuh"
 
@@ -339,7 +342,8 @@ size_t q2_block_bytes(int n, int nb, int m) {
 
 size_t unmtr_ws_bytes(int n, int nb, int m) {
   const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max(m, 1);
-  size_t b = nn * nb * sizeof(cplx) + 2 * (size_t)nb * mm * sizeof(cplx) + 3 * 256;
+  size_t b = 2 * nn * nb * sizeof(cplx) + 4 * (size_t)nb * mm * sizeof(cplx) + 6 * (size_t)nb * nb * sizeof(cplx) +
+             6 * 256;
   if (nb >= 2 && nb <= 64 && n > 2 * nb) b += q2_block_bytes(n, nb, m);
   return b;
 }
@@ -415,10 +419,13 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
   if (n <= 0 || m <= 0) return 0;
   Arena& ar = c.arena;
   const size_t save = ar.off;
-  cplx* V = ar.take<cplx>((size_t)n * nb);
-  cplx* W1 = ar.take<cplx>((size_t)nb * m);  // m x kr, ld m
-  cplx* W2 = ar.take<cplx>((size_t)nb * m);
-  if (!ar.ok() || !V) { ar.off = save; return GBHE_EWORKSPACE; }
+  cplx* V = ar.take<cplx>((size_t)n * 2 * nb);      // [V_{p-1} V_p], ld n
+  cplx* W1 = ar.take<cplx>((size_t)2 * nb * m);     // m x 2nb, ld m
+  cplx* W2 = ar.take<cplx>((size_t)2 * nb * m);
+  cplx* Tm = ar.take<cplx>((size_t)4 * nb * nb);    // 2nb x 2nb, ld 2nb
+  cplx* Gs = ar.take<cplx>((size_t)nb * nb);        // nb x nb
+  cplx* Ss = ar.take<cplx>((size_t)nb * nb);
+  if (!ar.ok() || !Ss) { ar.off = save; return GBHE_EWORKSPACE; }
   const size_t total = (size_t)n * m;
   k_promote<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, c.st>>>(Z, ldz, n, m, X, ldx);
   count_launch();
@@ -441,27 +448,59 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
     count_launch();
     GBHE_CUDA(cudaGetLastError());
   }
-  // ---- Q1
+  // ---- Q1, last panel first, in pairs (p-1, p)
   int npan = 0;
   for (int k = 0; k + nb < n; k += nb) ++npan;
   const cplx one = mk(1, 0), zero = mk(0, 0), mone = mk(-1, 0);
-  for (int p = npan - 1; p >= 0; --p) {
+  const size_t es = sizeof(cplx);
+  // explicit V of panel p (its mp rows, nb columns, ld n) at dst
+  auto vpanel = [&](int p, cplx* dst) {
     const int k = p * nb, mp = n - k - nb, kr = std::min(nb, mp);
-    k_panel_v<<<(int)std::min<size_t>(((size_t)mp * nb + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, k, nb, mp, kr, V, n);
+    k_panel_v<<<(int)std::min<size_t>(((size_t)mp * nb + 255) / 256, 4096), 256, 0, c.st>>>(A, lda, k, nb, mp, kr, dst,
+                                                                                           n);
     count_launch();
-    GBHE_CUDA(cudaGetLastError());
+    return cudaGetLastError() == cudaSuccess ? 0 : GBHE_ECUDA;
+  };
+  int rc = 0;
+  for (int p = npan - 1; p >= 0 && !rc; p -= 2) {
+    const int q = p - 1;                       // the pair (q, p), or p alone when q < 0
+    const int k = (q >= 0 ? q : p) * nb, mp = n - k - nb;
     cplx* Xr = X + (k + nb);
-    const cplx* T = T1 + (size_t)p * nb * nb;
-    int rc;
-    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, m, kr, mp, one, Xr, ldx, V, n, zero, W1, m), c.gemm_scratch,
-                    c.gemm_scratch_bytes))) { ar.off = save; return rc; }
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, m, kr, kr, one, W1, m, T, nb, zero, W2, m), nullptr, 0))) {
-      ar.off = save; return rc;
+    int w;                                     // block width
+    const cplx* Tb;                            // its T, ld ldt
+    int ldt;
+    if (q >= 0) {
+      w = 2 * nb;
+      if ((rc = vpanel(q, V))) break;
+      // V_p, nb rows lower in the second column block; its first nb rows are zero
+      GBHE_CUDA(cudaMemset2DAsync(V + (size_t)nb * n, es * n, 0, es * nb, nb, c.st));
+      if ((rc = vpanel(p, V + (size_t)nb * n + nb))) break;
+      const cplx* Tq = T1 + (size_t)q * nb * nb;
+      const cplx* Tp = T1 + (size_t)p * nb * nb;
+      // Tm = [[Tq, -Tq (Vq^H Vp) Tp], [0, Tp]]
+      if ((rc = zgemm(c, gemm_args(OP_C, OP_N, nb, nb, mp, one, V, n, V + (size_t)nb * n, n, zero, Gs, nb),
+                      c.gemm_scratch, c.gemm_scratch_bytes))) break;
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_N, nb, nb, nb, one, Gs, nb, Tp, nb, zero, Ss, nb), nullptr, 0))) break;
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_N, nb, nb, nb, mone, Tq, nb, Ss, nb, zero, Tm + (size_t)nb * 2 * nb,
+                                   2 * nb), nullptr, 0))) break;
+      GBHE_CUDA(cudaMemcpy2DAsync(Tm, es * 2 * nb, Tq, es * nb, es * nb, nb, cudaMemcpyDeviceToDevice, c.st));
+      GBHE_CUDA(cudaMemcpy2DAsync(Tm + (size_t)nb * 2 * nb + nb, es * 2 * nb, Tp, es * nb, es * nb, nb,
+                                  cudaMemcpyDeviceToDevice, c.st));
+      GBHE_CUDA(cudaMemset2DAsync(Tm + nb, es * 2 * nb, 0, es * nb, nb, c.st));
+      Tb = Tm;
+      ldt = 2 * nb;
+    } else {
+      w = std::min(nb, mp);
+      if ((rc = vpanel(p, V))) break;
+      Tb = T1 + (size_t)p * nb * nb;
+      ldt = nb;
     }
-    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, m, kr, mone, V, n, W2, m, one, Xr, ldx), nullptr, 0))) {
-      ar.off = save; return rc;
-    }
+    if ((rc = zgemm(c, gemm_args(OP_C, OP_N, m, w, mp, one, Xr, ldx, V, n, zero, W1, m), c.gemm_scratch,
+                    c.gemm_scratch_bytes))) break;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, m, w, w, one, W1, m, Tb, ldt, zero, W2, m), nullptr, 0))) break;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, mp, m, w, mone, V, n, W2, m, one, Xr, ldx), nullptr, 0))) break;
   }
+  if (rc) { ar.off = save; return rc; }
   ar.off = save;
   return 0;
 }
