@@ -621,8 +621,12 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
 // (reduce, stage bytes, write the residue tile) while the tensor cores work
 // on the next one.  Handshakes: per stage "empty" (MMA completion), per TMEM
 // buffer "full" (MMA completion) and "drained" (the 256 epilogue threads).
+// The epilogue stores each residue byte straight from its register to the
+// tile-major output layout (a warp covers 32 consecutive rows of one column:
+// one 32-byte segment per store), so no shared-memory staging tile is needed
+// and the shared memory goes to a deeper operand pipeline.
 // Grid and arguments as for k_crt_umma, 384 threads.
-constexpr int WS_STAGES = 4;
+constexpr int WS_STAGES = 6;
 constexpr int WS_THREADS = 384, WS_EPI = 256;
 
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
@@ -644,8 +648,7 @@ template <bool CPLX, int BN>
 struct WsCfg {
   static constexpr int NC = UCfg<CPLX, BN>::NC;
   static constexpr int STB = UCfg<CPLX, BN>::STB;
-  static constexpr int STILE = NC * BN * OPITCH;
-  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 2 * (size_t)STILE + 8 * (WS_STAGES + 5) + 16;
+  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 8 * (WS_STAGES + 5) + 16;
 };
 
 template <bool CPLX, int BN>
@@ -653,12 +656,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
                                                             int Kp, unsigned char* Out, const CrtDesc* D, int maxM,
                                                             int maxN, int lower, int mpc, int* status) {
   using CF = UCfg<CPLX, BN>;
-  using WF = WsCfg<CPLX, BN>;
   constexpr int NC = CF::NC;
   constexpr int STB = CF::STB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* stile0 = smem_raw + WS_STAGES * STB;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile0 + 2 * WF::STILE);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + WS_STAGES * STB);
   // bars: [0, S) stage empty, S + b accumulator full, S + 2 + b accumulator drained,
   // S + 4 drain of every issued MMA (before TMEM is freed)
   unsigned* tslot = reinterpret_cast<unsigned*>(bars + WS_STAGES + 5);
@@ -788,10 +789,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   } else {
     // ---------------- epilogue (256 threads): row 32 q + lane, columns NRES hh .. NRES hh + NRES - 1
     constexpr int NRES = CF::NRES;
-    const int q = w & 3, hh = (w - 4) >> 2, il = 32 * q + lane, et = t - 128;
+    const int q = w & 3, hh = (w - 4) >> 2, il = 32 * q + lane;
+    const bool row_ok = m0 + il < M;
+    // this thread's columns lie in one CBN-wide tile of the output layout
+    const int tile = ((BN / CBN) * by + (NRES * hh) / CBN) * TM + bx;
+    const int ct0 = (NRES * hh) % CBN;      // first column inside that tile
+    const int cv = N - n0 - NRES * hh;      // columns of this thread that exist
     for (int li = 0; li < mpc; ++li) {
       const int b = li & 1, l = l0 + li;
-      unsigned char* stile = stile0 + (li & 1) * WF::STILE;
+      unsigned char* obase = Out + ((size_t)tile * NMOD + l) * NC * OTILE + (size_t)ct0 * CBM + il;
       mbar_wait_cta(smem_addr(bars + WS_STAGES + b), (unsigned)(li >> 1) & 1u, sabort, status);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float p = (float)c_p[l], pinv = c_pinv[l];
@@ -808,20 +814,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
           for (int x = 0; x < 16; ++x) {
             float v = red_sym(P[c][x], p, pinv);  // |v| <= p/2 + 1
             if (v < 0.f) v += p;                  // [0, p)
-            stile[(c * BN + NRES * hh + sl * 16 + x) * OPITCH + il] = (unsigned char)(int)v;
+            if (row_ok && sl * 16 + x < cv)
+              obase[(size_t)c * OTILE + (size_t)(sl * 16 + x) * CBM] = (unsigned char)(int)v;
           }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_addr(bars + WS_STAGES + 2 + b));  // buffer b may be overwritten
-      named_sync(2, WS_EPI);
-      const int nu = (min(UBM, M - m0) + 15) / 16, ncol = min(BN, N - n0);
-      for (int i = et; i < NC * ncol * nu; i += WS_EPI) {
-        const int c = i / (ncol * nu), rem = i % (ncol * nu), jl = rem / nu, uu = rem % nu;
-        const int tile = ((BN / CBN) * by + jl / CBN) * TM + bx;
-        unsigned char* dst = Out + ((size_t)tile * NMOD + l) * NC * OTILE;
-        const uint4 v = *reinterpret_cast<const uint4*>(stile + (c * BN + jl) * OPITCH + uu * 16);
-        *reinterpret_cast<uint4*>(dst + ((size_t)c * CBN + (jl % CBN)) * CBM + uu * 16) = v;
-      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
