@@ -615,19 +615,22 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
 
 // Warp-specialised form for products whose moduli are each one exact chunk
 // (Kp <= KC_TERMS: the K <= 256 updates of the blocked factorisations, the
-// panel updates and the Q2 block reflectors).  Warps 0-3 stage operands with
-// cp.async and thread 0 issues the MMAs; warps 4-11 (two per TMEM lane
-// quarter, 64 columns each) drain the TMEM buffer of the previous modulus
-// (reduce, stage bytes, write the residue tile) while the tensor cores work
-// on the next one.  Handshakes: per stage "empty" (MMA completion), per TMEM
-// buffer "full" (MMA completion) and "drained" (the 256 epilogue threads).
+// panel updates and the back-transform's block reflectors).  Warps 0-3 stage
+// operands with cp.async, warp 4 issues the MMAs (one lane), warps 5-12 (two
+// per TMEM lane quarter) drain the TMEM buffer of the previous modulus while
+// the tensor cores work on the next one.  Handshakes: per stage "ready" (the
+// 128 producers, each after its own copies of the stage completed and were
+// fenced for the tensor cores) and "empty" (MMA completion), per TMEM buffer
+// "full" (MMA completion) and "drained" (the 256 epilogue threads).  The
+// producers run WS_LAG stages ahead of the stage they report ready, so the
+// MMA warp never waits on the producers' refill of the stage it just read.
 // The epilogue stores each residue byte straight from its register to the
 // tile-major output layout (a warp covers 32 consecutive rows of one column:
 // one 32-byte segment per store), so no shared-memory staging tile is needed
 // and the shared memory goes to a deeper operand pipeline.
 // Grid and arguments as for k_crt_umma, 384 threads.
-constexpr int WS_STAGES = 6;
-constexpr int WS_THREADS = 384, WS_EPI = 256;
+constexpr int WS_STAGES = 6, WS_LAG = 3;
+constexpr int WS_THREADS = 416, WS_EPI = 256;
 
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
@@ -648,7 +651,7 @@ template <bool CPLX, int BN>
 struct WsCfg {
   static constexpr int NC = UCfg<CPLX, BN>::NC;
   static constexpr int STB = UCfg<CPLX, BN>::STB;
-  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 8 * (WS_STAGES + 5) + 16;
+  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 8 * (2 * WS_STAGES + 5) + 16;
 };
 
 template <bool CPLX, int BN>
@@ -661,8 +664,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + WS_STAGES * STB);
   // bars: [0, S) stage empty, S + b accumulator full, S + 2 + b accumulator drained,
-  // S + 4 drain of every issued MMA (before TMEM is freed)
-  unsigned* tslot = reinterpret_cast<unsigned*>(bars + WS_STAGES + 5);
+  // S + 4 drain of every issued MMA (before TMEM is freed), S + 5 + s stage ready
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2 * WS_STAGES + 5);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + BN - 1) / BN;
@@ -696,6 +699,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + WS_STAGES + 4)));
     for (int i = 0; i < 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + WS_STAGES + 2 + i)), "r"(WS_EPI));
+    for (int i = 0; i < WS_STAGES; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + WS_STAGES + 5 + i)), "r"(128));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sabort = 0;
   }
@@ -712,9 +717,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   const int iters = mpc * ktiles;
 
   if (w < 4) {
-    // ---------------- producers (128 threads); thread 0 also issues the MMAs
-    const unsigned idesc = (1u << 4) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
-    const unsigned idesc_negA = idesc | (1u << 13);
+    // ---------------- producers (128 threads)
     auto load = [&](int it) {
       unsigned char* sA = smem_raw + (it % WS_STAGES) * STB;
       unsigned char* sB = sA + NC * U_APL;
@@ -736,22 +739,37 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
         cp16(sB + c * CF::BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
       }
     };
-#pragma unroll
-    for (int s = 0; s < WS_STAGES - 1; ++s) {
-      if (s < iters) load(s);
+    // my copies of stage `it` are complete: fence them for the tensor cores and report
+    auto ready = [&](int it) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_addr(bars + WS_STAGES + 5 + it % WS_STAGES));
+    };
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % WS_STAGES;
+      if (it >= WS_STAGES)  // the MMAs of iteration it - S have read the stage
+        mbar_wait_cta(smem_addr(bars + s), (unsigned)((it / WS_STAGES) - 1) & 1u, sabort, status);
+      load(it);
       cp_commit();
+      if (it >= WS_LAG) {
+        cp_wait<WS_LAG>();  // every group but the newest WS_LAG is complete
+        ready(it - WS_LAG);
+      }
     }
+    cp_wait<0>();
+    for (int it = std::max(0, iters - WS_LAG); it < iters; ++it) ready(it);
+  } else if (w == 4) {
+    // ---------------- MMA issue (one lane of warp 4)
+    const unsigned idesc = (1u << 4) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
+    const unsigned idesc_negA = idesc | (1u << 13);
     for (int it = 0; it < iters; ++it) {
       const int s = it % WS_STAGES;
       const int li = it / ktiles, kt = it % ktiles, b = li & 1;
-      cp_wait<WS_STAGES - 2>();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      named_sync(1, 128);
-      if (t == 0) {
-        // buffer b must have been drained by the epilogue of modulus li - 2
-        if (kt == 0 && li >= 2)
-          mbar_wait_cta(smem_addr(bars + WS_STAGES + 2 + b), (unsigned)((li - 2) >> 1) & 1u, sabort, status);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // buffer b must have been drained by the epilogue of modulus li - 2
+      if (kt == 0 && li >= 2)
+        mbar_wait_cta(smem_addr(bars + WS_STAGES + 2 + b), (unsigned)((li - 2) >> 1) & 1u, sabort, status);
+      mbar_wait_cta(smem_addr(bars + WS_STAGES + 5 + s), (unsigned)(it / WS_STAGES) & 1u, sabort, status);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (lane == 0) {
         const unsigned dbuf = tmem + (unsigned)b * CF::BUFC;
         const unsigned sA = smem_addr(smem_raw + s * STB), sB = sA + NC * U_APL;
 #pragma unroll
@@ -771,25 +789,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
         umma_commit(smem_addr(bars + s));
         if (kt == ktiles - 1) umma_commit(smem_addr(bars + WS_STAGES + b));
       }
-      if (it + WS_STAGES - 1 < iters) {
-        if (it >= 1)
-          mbar_wait_cta(smem_addr(bars + (it - 1) % WS_STAGES), (unsigned)((it - 1) / WS_STAGES) & 1u, sabort,
-                        status);
-        load(it + WS_STAGES - 1);
-      }
-      cp_commit();
+      __syncwarp();
     }
-    cp_wait<0>();
     // every MMA issued here has completed before TMEM is freed (bounded wait;
     // also when a timeout made the other waits give up)
-    if (t == 0) {
+    if (lane == 0) {
       umma_commit(smem_addr(bars + WS_STAGES + 4));
       if (!mbar_wait(smem_addr(bars + WS_STAGES + 4), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
     }
+    __syncwarp();
   } else {
-    // ---------------- epilogue (256 threads): row 32 q + lane, columns NRES hh .. NRES hh + NRES - 1
+    // ---------------- epilogue (warps 5-12): row 32 q + lane, columns NRES hh .. NRES hh + NRES - 1
     constexpr int NRES = CF::NRES;
-    const int q = w & 3, hh = (w - 4) >> 2, il = 32 * q + lane;
+    const int q = w & 3, hh = (w - 5) >> 2, il = 32 * q + lane;
     const bool row_ok = m0 + il < M;
     // this thread's columns lie in one CBN-wide tile of the output layout
     const int tile = ((BN / CBN) * by + (NRES * hh) / CBN) * TM + bx;
