@@ -1,6 +1,8 @@
 // dense.cu -- Algorithm 1 steps 1, 2 and 4 of the paper (Section 3):
 //   potrf  B = L L^H                (blocked right-looking Cholesky)
-//   hegst  A' = L^{-1} A L^{-H}     (two blocked forward solves)
+//   hegst  A' = L^{-1} A L^{-H}     (blocked two-sided reduction: per block
+//                                    column a rank-2 trailing update and a
+//                                    thin forward solve, about 4 n^3 flops)
 //   trsm   X = L^{-1} X  or  X = L^{-H} X
 // The diagonal blocks (DB x DB) are factored / inverted by one CTA each in
 // shared memory; everything else is DMMA GEMM (gemm.cu).
@@ -114,43 +116,6 @@ __global__ void k_fill_upper(cplx* A, int lda, int n) {
   }
 }
 
-// In-place conjugate transpose of the square n x n A (tiled 32 x 32 swaps).
-__global__ void k_conj_transpose(cplx* A, int lda, int n) {
-  __shared__ cplx t1[32][33], t2[32][33];
-  const int bi = blockIdx.x, bj = blockIdx.y;
-  if (bi < bj) return;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int k = ty; k < 32; k += 8) {
-    int r = bi * 32 + tx, c = bj * 32 + k;
-    if (r < n && c < n) t1[k][tx] = A[(size_t)r + (size_t)c * lda];
-    r = bj * 32 + tx; c = bi * 32 + k;
-    if (r < n && c < n) t2[k][tx] = A[(size_t)r + (size_t)c * lda];
-  }
-  __syncthreads();
-  for (int k = ty; k < 32; k += 8) {
-    // element (bj*32+tx, bi*32+k) <- conj(old (bi*32+k, bj*32+tx)) = conj(t1[tx][k])
-    int r = bj * 32 + tx, c = bi * 32 + k;
-    if (r < n && c < n) A[(size_t)r + (size_t)c * lda] = cconj(t1[tx][k]);
-    r = bi * 32 + tx; c = bj * 32 + k;
-    if (bi != bj && r < n && c < n) A[(size_t)r + (size_t)c * lda] = cconj(t2[tx][k]);
-  }
-}
-
-// A := (Y + Y^H)/2 for the square Y stored in A (both triangles written).
-__global__ void k_hermitize(cplx* A, int lda, int n) {
-  const size_t total = (size_t)n * n;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int r = (int)(i % n), c = (int)(i / n);
-    if (r < c) continue;
-    cplx a = A[(size_t)r + (size_t)c * lda], b = A[(size_t)c + (size_t)r * lda];
-    cplx v = mk(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-    if (r == c) v.y = 0.0;
-    A[(size_t)r + (size_t)c * lda] = v;
-    A[(size_t)c + (size_t)r * lda] = cconj(v);
-  }
-}
-
 int diag_smem() { return 2 * DB * DB * (int)sizeof(cplx); }
 
 int ensure_attrs() {
@@ -175,13 +140,14 @@ inline int grid1d(size_t total, int threads = 256) {
 // diagonal blocks are factored / inverted with the 64-wide kernels above.
 constexpr int TB = 256;
 
-// Layout of the dense scratch: 64-block inverses | TB-block inverses | temp.
+// Layout of the dense scratch: 64-block inverses | TB-block inverses | temp
+// (n x TB) | the hegst panel buffer [A21 L21 A21] (n x 3 TB).
 size_t inv64_elems(int n) { return (size_t)((n + DB - 1) / DB) * DB * DB; }
 size_t invtb_elems(int n) { return (size_t)((n + TB - 1) / TB) * TB * TB; }
 
 size_t dense_ws_bytes(int n) {
   const size_t nn = (size_t)std::max(n, 1);
-  return (inv64_elems(n) + invtb_elems(n) + nn * TB) * sizeof(cplx) + 3 * 256;
+  return (inv64_elems(n) + invtb_elems(n) + nn * TB + nn * 3 * TB) * sizeof(cplx) + 4 * 256;
 }
 
 namespace {
@@ -189,6 +155,9 @@ namespace {
 cplx* inv64_buf(Ctx& c) { return c.dense_scratch; }
 cplx* invtb_buf(Ctx& c, int n) { return c.dense_scratch + inv64_elems(n); }
 cplx* temp_buf(Ctx& c, int n) { return c.dense_scratch + inv64_elems(n) + invtb_elems(n); }
+cplx* panel3_buf(Ctx& c, int n) {
+  return c.dense_scratch + inv64_elems(n) + invtb_elems(n) + (size_t)std::max(n, 1) * TB;
+}
 
 __global__ void k_set_identity(cplx* X, int ldx, int bs) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < bs * bs; q += gridDim.x * blockDim.x) {
@@ -336,21 +305,72 @@ int trsm_run(Ctx& c, int trans, int n, int m, const cplx* L, int ldl, cplx* X, i
   return 0;
 }
 
+// Blocked two-sided reduction A' = L^{-1} A L^{-H} (lower storage), block
+// column b of order bs at k0 (the standard right-looking scheme):
+//   A11 <- L11^{-1} A11 L11^{-H}
+//   A21 <- A21 L11^{-H};  A21 -= 1/2 L21 A11
+//   A22 -= A21 L21^H + L21 A21^H          (lower; one product [A21 L21][L21 A21]^H)
+//   A21 -= 1/2 L21 A11;   A21 <- L22^{-1} A21
+// with every TB x TB diagonal block of L inverted once up front.  The upper
+// triangle of A is never read; on return it holds the mirror of the lower.
 int hegst_run(Ctx& c, int n, cplx* A, int lda, const cplx* L, int ldl) {
   if (n <= 0) return 0;
+  int rc = ensure_attrs();
+  if (rc) return rc;
+  const int nblk = (n + TB - 1) / TB;
+  cplx* Linv = invtb_buf(c, n);
+  for (int b = 0; b < nblk; ++b) {
+    const int k0 = b * TB, bs = std::min(TB, n - k0);
+    if ((rc = trtri_block(c, bs, L + (size_t)k0 + (size_t)k0 * ldl, ldl, Linv + (size_t)b * TB * TB))) return rc;
+  }
+  cplx* T = temp_buf(c, n);
+  cplx* P3 = panel3_buf(c, n);
+  const cplx one = mk(1, 0), zero = mk(0, 0), mone = mk(-1, 0), mhalf = mk(-0.5, 0);
+  for (int b = 0; b < nblk; ++b) {
+    const int k0 = b * TB, bs = std::min(TB, n - k0), rest = n - k0 - bs;
+    cplx* A11 = A + (size_t)k0 + (size_t)k0 * lda;
+    const cplx* Lb = Linv + (size_t)b * TB * TB;
+    // A11 <- Lb A11 Lb^H (A11 read Hermitian from its lower triangle, written as a full square)
+    if ((rc = zgemm(c, gemm_args(OP_H, OP_C, bs, bs, bs, one, A11, lda, Lb, TB, zero, T, bs), nullptr, 0))) return rc;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, bs, bs, bs, one, Lb, TB, T, bs, zero, A11, lda), nullptr, 0))) return rc;
+    if (rest <= 0) break;
+    cplx* A21 = A + (size_t)(k0 + bs) + (size_t)k0 * lda;
+    const cplx* L21 = L + (size_t)(k0 + bs) + (size_t)k0 * ldl;
+    cplx* A22 = A + (size_t)(k0 + bs) + (size_t)(k0 + bs) * lda;
+    // A21 <- A21 Lb^H (through the temporary), then A21 -= 1/2 L21 A11
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, rest, bs, bs, one, A21, lda, Lb, TB, zero, T, rest), nullptr, 0)))
+      return rc;
+    k_copy_block<<<1024, 256, 0, c.st>>>(T, rest, A21, lda, rest, bs);
+    count_launch();
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, rest, bs, bs, mhalf, L21, ldl, A11, lda, one, A21, lda), nullptr, 0)))
+      return rc;
+    // A22 -= [A21 L21] [L21 A21]^H (lower), from the buffer [A21 L21 A21] (ld rest)
+    k_copy_block<<<1024, 256, 0, c.st>>>(A21, lda, P3, rest, rest, bs);
+    k_copy_block<<<1024, 256, 0, c.st>>>(L21, ldl, P3 + (size_t)bs * rest, rest, rest, bs);
+    k_copy_block<<<1024, 256, 0, c.st>>>(A21, lda, P3 + (size_t)2 * bs * rest, rest, rest, bs);
+    count_launch(3);
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_C, rest, rest, 2 * bs, mone, P3, rest, P3 + (size_t)bs * rest, rest, one,
+                                 A22, lda, 1), nullptr, 0)))
+      return rc;
+    if ((rc = zgemm(c, gemm_args(OP_N, OP_N, rest, bs, bs, mhalf, L21, ldl, A11, lda, one, A21, lda), nullptr, 0)))
+      return rc;
+    // A21 <- L22^{-1} A21: forward solve over the following diagonal blocks
+    for (int bb = b + 1; bb < nblk; ++bb) {
+      const int off = bb * TB - (k0 + bs), bsb = std::min(TB, n - bb * TB), rest2 = rest - off - bsb;
+      cplx* Xb = A21 + off;
+      if ((rc = zgemm(c, gemm_args(OP_N, OP_N, bsb, bs, bsb, one, Linv + (size_t)bb * TB * TB, TB, Xb, lda, zero, T,
+                                   TB), nullptr, 0)))
+        return rc;
+      k_copy_block<<<1024, 256, 0, c.st>>>(T, TB, Xb, lda, bsb, bs);
+      count_launch();
+      if (rest2 > 0)
+        if ((rc = zgemm(c, gemm_args(OP_N, OP_N, rest2, bs, bsb, mone, L + (size_t)(bb * TB + bsb) + (size_t)(bb * TB) * ldl,
+                                     ldl, Xb, lda, one, Xb + bsb, lda), nullptr, 0)))
+          return rc;
+    }
+  }
   const size_t total = (size_t)n * n;
   k_fill_upper<<<grid1d(total), 256, 0, c.st>>>(A, lda, n);
-  count_launch();
-  GBHE_CUDA(cudaGetLastError());
-  int rc = trsm_run(c, 0, n, n, L, ldl, A, lda);  // W = L^{-1} A
-  if (rc) return rc;
-  dim3 tg((n + 31) / 32, (n + 31) / 32);
-  k_conj_transpose<<<tg, dim3(32, 8), 0, c.st>>>(A, lda, n);  // W^H
-  GBHE_CUDA(cudaGetLastError());
-  count_launch();
-  rc = trsm_run(c, 0, n, n, L, ldl, A, lda);  // L^{-1} W^H = A'^H
-  if (rc) return rc;
-  k_hermitize<<<grid1d(total), 256, 0, c.st>>>(A, lda, n);
   count_launch();
   GBHE_CUDA(cudaGetLastError());
   return 0;
