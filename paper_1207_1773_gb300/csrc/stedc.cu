@@ -342,13 +342,22 @@ __global__ void __launch_bounds__(128) k_gather(DC a, int lev) {
 }
 
 // ---------------------------------------------------------------- secular
+// Sums over the k poles, split across the 32 lanes of a warp; every lane ends
+// with the totals (butterfly reductions), so the whole warp takes the same
+// iteration decisions.
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ void secular_eval(const double* D, const double* z, int k, int org, double rho, double tau,
-                             int split, double& g, double& psi, double& dpsi, double& phi, double& dphi,
+                             int split, int lane, double& g, double& psi, double& dpsi, double& phi, double& dphi,
                              double& erretm) {
   psi = dpsi = phi = dphi = 0.0;
   erretm = 0.0;
   const double Do = D[org];
-  for (int j = 0; j < k; ++j) {
+  for (int j = lane; j < k; j += 32) {
     const double del = (D[j] - Do) - tau;
     const double tmp = z[j] / del;
     const double term = rho * z[j] * tmp;
@@ -356,14 +365,19 @@ __device__ void secular_eval(const double* D, const double* z, int k, int org, d
     else { phi += term; dphi += rho * tmp * tmp; }
     erretm += fabs(term);
   }
+  psi = warp_allsum(psi);
+  dpsi = warp_allsum(dpsi);
+  phi = warp_allsum(phi);
+  dphi = warp_allsum(dphi);
+  erretm = warp_allsum(erretm);
   g = 1.0 + psi + phi;
 }
 
-// One thread per root.  Root i lies in (D_i, D_{i+1}) (i < k-1) or
+// One warp per root.  Root i lies in (D_i, D_{i+1}) (i < k-1) or
 // (D_{k-1}, D_{k-1} + rho |z|^2] (i = k-1).
 __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
   if (dc_failed(a)) return;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (g >= a.n) return;
   NodeR nd;
   node_of(a, lev, g, nd);
@@ -376,9 +390,11 @@ __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
   const double* z = a.ndz + lo;
   const double rho = 2.0 * fabs(a.ee[nd.mid - 1]);
   if (k == 1) {
-    a.rorg[lo] = 0;
-    a.rtau[lo] = rho * z[0] * z[0];
-    a.rlam[lo] = D[0] + rho * z[0] * z[0];
+    if (lane == 0) {
+      a.rorg[lo] = 0;
+      a.rtau[lo] = rho * z[0] * z[0];
+      a.rlam[lo] = D[0] + rho * z[0] * z[0];
+    }
     return;
   }
   int org, split;
@@ -387,14 +403,16 @@ __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
     const double del = D[i + 1] - D[i];
     const double mid = 0.5 * del;
     // f(D_i + del/2) > 0  <=>  root below the midpoint
-    double fm = 1.0;
-    for (int j = 0; j < k; ++j) fm += rho * z[j] * z[j] / ((D[j] - D[i]) - mid);
+    double fm = 0.0;
+    for (int j = lane; j < k; j += 32) fm += rho * z[j] * z[j] / ((D[j] - D[i]) - mid);
+    fm = 1.0 + warp_allsum(fm);
     if (fm >= 0.0) { org = i; lo_t = 0.0; hi_t = mid; }
     else { org = i + 1; lo_t = -mid; hi_t = 0.0; }
     split = i;
   } else {
     double zz = 0.0;
-    for (int j = 0; j < k; ++j) zz += z[j] * z[j];
+    for (int j = lane; j < k; j += 32) zz += z[j] * z[j];
+    zz = warp_allsum(zz);
     org = k - 1; lo_t = 0.0; hi_t = rho * zz; split = k - 1;
   }
   const double dl = D[i] - D[org];                       // left pole (relative)
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
   int it;
   for (it = 0; it < 200; ++it) {
     double gv, psi, dpsi, phi, dphi, erretm;
-    secular_eval(D, z, k, org, rho, x, split, gv, psi, dpsi, phi, dphi, erretm);
+    secular_eval(D, z, k, org, rho, x, split, lane, gv, psi, dpsi, phi, dphi, erretm);
     if (fabs(gv) <= 8.0 * EPS * (1.0 + erretm) * (double)k) break;
     if (gv > 0.0) hi_t = x; else lo_t = x;
     if (hi_t - lo_t <= 2.0 * EPS * fmax(fabs(lo_t), fabs(hi_t))) break;
@@ -438,6 +456,7 @@ __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
     if (!(y > lo_t && y < hi_t)) y = 0.5 * (lo_t + hi_t);
     x = y;
   }
+  if (lane != 0) return;
   if (it >= 200) set_err_once(a.st, GBHE_ENOTCONV);
   a.rorg[lo + i] = org;
   a.rtau[lo + i] = x;
@@ -445,9 +464,10 @@ __global__ void __launch_bounds__(128) k_secular(DC a, int lev) {
 }
 
 // ---------------------------------------------------------------- zhat
+// One warp per pole j; the product over i != j is split across the lanes.
 __global__ void __launch_bounds__(128) k_zhat(DC a, int lev) {
   if (dc_failed(a)) return;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (g >= a.n) return;
   NodeR nd;
   node_of(a, lev, g, nd);
@@ -459,19 +479,21 @@ __global__ void __launch_bounds__(128) k_zhat(DC a, int lev) {
   const double rho = 2.0 * fabs(a.ee[nd.mid - 1]);
   // zhat_j^2 = (lambda_j - d_j)/rho * prod_{i != j} (lambda_i - d_j)/(d_i - d_j)
   const double dj = D[j];
-  double p = -((dj - D[a.rorg[lo + j]]) - a.rtau[lo + j]) / rho;
-  for (int i = 0; i < k; ++i) {
+  double p = 1.0;
+  for (int i = lane; i < k; i += 32) {
     if (i == j) continue;
     const double lmd = -((dj - D[a.rorg[lo + i]]) - a.rtau[lo + i]);  // lambda_i - d_j
     p *= lmd / (D[i] - dj);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) p *= __shfl_xor_sync(0xffffffffu, p, o);
+  if (lane != 0) return;
+  p *= -((dj - D[a.rorg[lo + j]]) - a.rtau[lo + j]) / rho;
   const double zj = a.ndz[lo + j];
   const double v = sqrt(fabs(p));
   a.zhat[lo + j] = (zj >= 0.0) ? v : -v;
 }
 
-// ---------------------------------------------------------------- qbuild
-// One warp per root column i: Q(gemm_pos(j), i) = zhat_j/(d_j - lambda_i), normalised.
 __global__ void __launch_bounds__(128) k_qbuild(DC a, int lev) {
   if (dc_failed(a)) return;
   const int g = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -712,9 +734,9 @@ int stedc_run(Ctx& c, int n, const double* d, const double* e, int il, int iu, d
     count_launch();
     k_gather<<<n, 128, 0, c.st>>>(a, lev);
     count_launch();
-    k_secular<<<(n + 127) / 128, 128, 0, c.st>>>(a, lev);
+    k_secular<<<(n + 3) / 4, 128, 0, c.st>>>(a, lev);
     count_launch();
-    k_zhat<<<(n + 127) / 128, 128, 0, c.st>>>(a, lev);
+    k_zhat<<<(n + 3) / 4, 128, 0, c.st>>>(a, lev);
     count_launch();
     k_qbuild<<<(n + 3) / 4, 128, 0, c.st>>>(a, lev);
     count_launch();
