@@ -254,13 +254,12 @@ int gbhe_gemm_crt(gbhe_handle h, int cplx, int opA, int opB, int m, int n, int k
 /* The number-theory tables of that engine, exactly as copied to the device
  * (host-only, no CUDA call): moduli p[16]; CRT weights W[16][4], W_l =
  * (M/p_l) * ((M/p_l)^-1 mod p_l) mod M as 128-bit little-endian 32-bit words;
- * M[4] = prod p_l, likewise; k18[16], k36[16] = 2^18, 2^36 mod p_l (limb
- * weights of the residue split); bm[16] = floor(2^32 / p_l) (Barrett
- * reduction); frac[16] = y_l / p_l rounded to float, y_l = (M/p_l)^-1 mod p_l
- * (the FP32 estimate of the reconstruction's multiple of M).  Any pointer may
- * be NULL.  Returns the number of moduli. */
-int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, unsigned* k18, unsigned* k36, unsigned* bm,
-                    float* frac);
+ * M[4] = prod p_l, likewise; k13[16], k26[16], k39[16] = the symmetric
+ * residues (in [-p/2, p/2]) of 2^13, 2^26, 2^39 modulo p_l (the limb weights
+ * of the FP32 residue split); frac[16] = y_l / p_l rounded to float, y_l =
+ * (M/p_l)^-1 mod p_l (the FP32 estimate of the reconstruction's multiple of
+ * M).  Any pointer may be NULL.  Returns the number of moduli. */
+int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, int* k13, int* k26, int* k39, float* frac);
 
 /* The complex DMMA GEMM of gbhe_zgemm (same operand modes and arguments, no
  * handle) for callers that cannot allocate: code that must not take device

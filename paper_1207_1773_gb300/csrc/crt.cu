@@ -11,6 +11,9 @@
 //   2. Residues.  The integers are reduced modulo NMOD = 16 pairwise coprime
 //      moduli p_l <= 256 (product M ~ 2^125) to symmetric residues |r| <= 128,
 //      exact in FP16.  Complex operands give two planes (Re, Im) per modulus.
+//      The reduction runs in FP32 on exact integers: four signed 13-bit limbs
+//      of v, t = l0 + l1 w1 + l2 w2 + l3 w3 with w_i the symmetric residues of
+//      2^(13 i) (|t| < 2^23), r = t - p rint(t / p) (|r| <= p/2 + 1 <= 128).
 //   3. Products.  For each modulus the residue products run on tcgen05.mma
 //      kind::f16 (f16 -> f32 accumulators in tensor memory): real operands
 //      one product, complex operands Re C = Ar Br - Ai Bi and
@@ -48,8 +51,7 @@ __constant__ float c_pinv[NMOD];
 __constant__ float c_frac[NMOD];         // y_l / p_l
 __constant__ unsigned c_W[NMOD][4];      // W_l (128-bit, little-endian words)
 __constant__ unsigned c_M[4];            // M
-__constant__ unsigned c_k18[NMOD], c_k36[NMOD];  // 2^18 mod p, 2^36 mod p
-__constant__ unsigned c_bm[NMOD];                // floor(2^32 / p) (Barrett reduction)
+__constant__ float c_kw[NMOD][3];        // symmetric residues of 2^13, 2^26, 2^39 mod p (limb weights)
 
 bool g_const_ready[MAX_DEVICES] = {};
 
@@ -60,7 +62,7 @@ struct HostTables {
   int p[NMOD];
   float pinv[NMOD], frac[NMOD];
   unsigned W[NMOD][4], M[4];
-  unsigned k18[NMOD], k36[NMOD], bm[NMOD];
+  int kw[NMOD][3];  // symmetric residues of 2^13, 2^26, 2^39 modulo p_l
 };
 
 void crt_tables(HostTables& t) {
@@ -79,9 +81,10 @@ void crt_tables(HostTables& t) {
     t.p[l] = pl;
     t.pinv[l] = 1.0f / (float)pl;
     t.frac[l] = (float)((double)y / (double)pl);
-    t.k18[l] = (unsigned)(((u128)1 << 18) % (u128)pl);
-    t.k36[l] = (unsigned)(((u128)1 << 36) % (u128)pl);
-    t.bm[l] = (unsigned)(((u128)1 << 32) / (u128)pl);
+    for (int i = 0; i < 3; ++i) {
+      const int r = (int)(((u128)1 << (13 * (i + 1))) % (u128)pl);
+      t.kw[l][i] = r > pl / 2 ? r - pl : r;
+    }
   }
   for (int w = 0; w < 4; ++w) t.M[w] = (unsigned)(M >> (32 * w));
 }
@@ -97,9 +100,10 @@ int init_constants() {
   GBHE_CUDA(cudaMemcpyToSymbol(c_frac, t.frac, sizeof(t.frac)));
   GBHE_CUDA(cudaMemcpyToSymbol(c_W, t.W, sizeof(t.W)));
   GBHE_CUDA(cudaMemcpyToSymbol(c_M, t.M, sizeof(t.M)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_k18, t.k18, sizeof(t.k18)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_k36, t.k36, sizeof(t.k36)));
-  GBHE_CUDA(cudaMemcpyToSymbol(c_bm, t.bm, sizeof(t.bm)));
+  float kw[NMOD][3];
+  for (int l = 0; l < NMOD; ++l)
+    for (int i = 0; i < 3; ++i) kw[l][i] = (float)t.kw[l][i];
+  GBHE_CUDA(cudaMemcpyToSymbol(c_kw, kw, sizeof(kw)));
   g_const_ready[dev] = true;
   return 0;
 }
@@ -199,9 +203,8 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
   const int r = r0 + q, k = k0 + kq;
   if (r >= o.R) return;
   const int er = e[r];
-  // scaled integers (|v| <= 2^52) as sign + three 18-bit limbs
-  bool sg[4][2];
-  unsigned a[4][2], b[4][2], c[4][2];
+  // scaled integers (|v| <= 2^52) as four signed 13-bit limbs, exact in FP32
+  float lim[4][2][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const double2 v = tile[q][kq + u];
@@ -216,28 +219,26 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
         const int sh = er - (E - 1023);  // right shift (>= 1)
         if (sh <= 60) mag = (mant + (1ull << (sh - 1))) >> sh;
       }
-      sg[u][part] = bits < 0;
-      a[u][part] = (unsigned)(mag >> 36);
-      b[u][part] = (unsigned)((mag >> 18) & 0x3FFFF);
-      c[u][part] = (unsigned)(mag & 0x3FFFF);
+      const float sg = bits < 0 ? -1.f : 1.f;
+      lim[u][part][0] = sg * (float)(unsigned)(mag & 0x1FFFu);
+      lim[u][part][1] = sg * (float)(unsigned)((mag >> 13) & 0x1FFFu);
+      lim[u][part][2] = sg * (float)(unsigned)((mag >> 26) & 0x1FFFu);
+      lim[u][part][3] = sg * (float)(unsigned)(mag >> 39);  // <= 2^13
     }
   }
 #pragma unroll
   for (int l = 0; l < NMOD; ++l) {
-    const unsigned p = (unsigned)c_p[l], bm = c_bm[l], k18 = c_k18[l], k36 = c_k36[l];
+    const float p = (float)c_p[l], pinv = c_pinv[l], w1 = c_kw[l][0], w2 = c_kw[l][1], w3 = c_kw[l][2];
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
       if (part == 1 && !o.cplx) break;
       __half hv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        // t = mag mod-equivalent below 2^27; Barrett: t - p floor(t bm / 2^32) lies in [0, 2p)
-        const unsigned tt = a[u][part] * k36 + b[u][part] * k18 + c[u][part];
-        unsigned rr = tt - __umulhi(tt, bm) * p;
-        if (rr >= p) rr -= p;
-        int sv = rr > (p >> 1) ? (int)rr - (int)p : (int)rr;  // symmetric, |sv| <= 128
-        if (sg[u][part]) sv = -sv;
-        hv[u] = __int2half_rn(sv);
+        // t = v mod-equivalent, an integer below 2^23 (every partial sum exact)
+        const float t = fmaf(lim[u][part][3], w3, fmaf(lim[u][part][2], w2, fmaf(lim[u][part][1], w1,
+                                                                                   lim[u][part][0])));
+        hv[u] = __float2half_rn(fmaf(-rintf(t * pinv), p, t));  // symmetric, |r| <= 128: exact in FP16
       }
       // Kp is a multiple of 32 and k of 4: the 8-byte store is aligned and in the row
       __half* dst = P + (size_t)(l * ncomp + part) * plane + (size_t)r * Kp + k;
@@ -1299,16 +1300,15 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
 
 }  // namespace gbhe
 
-extern "C" int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, unsigned* k18, unsigned* k36, unsigned* bm,
-                               float* frac) {
+extern "C" int gbhe_crt_tables(int* p, unsigned* W, unsigned* M, int* k13, int* k26, int* k39, float* frac) {
   gbhe::HostTables t;
   gbhe::crt_tables(t);
   for (int l = 0; l < gbhe::NMOD; ++l) {
     if (p) p[l] = t.p[l];
     if (frac) frac[l] = t.frac[l];
-    if (k18) k18[l] = t.k18[l];
-    if (k36) k36[l] = t.k36[l];
-    if (bm) bm[l] = t.bm[l];
+    if (k13) k13[l] = t.kw[l][0];
+    if (k26) k26[l] = t.kw[l][1];
+    if (k39) k39[l] = t.kw[l][2];
     for (int w = 0; w < 4; ++w)
       if (W) W[4 * l + w] = t.W[l][w];
   }

@@ -418,16 +418,16 @@ PROF_CLASSES = {"zgemm": 0, "dgemm": 1, "panel": 2, "chase": 3, "q2": 4, "stedc"
 
 
 def crt_tables():
-    """The tensor-core FP64 engine's tables (host-only): dict of p, W, M, k18,
-    k36, bm as Python ints (W and M joined from their 32-bit words) and frac
-    as the float32 values the device uses."""
+    """The tensor-core FP64 engine's tables (host-only): dict of p, W, M as
+    Python ints (W and M joined from their 32-bit words), the signed limb
+    weights k13, k26, k39 and frac as the float32 values the device uses."""
     k = 16
     p = (ctypes.c_int * k)()
     W = (ctypes.c_uint * (4 * k))()
     M = (ctypes.c_uint * 4)()
-    k18, k36, bm = (ctypes.c_uint * k)(), (ctypes.c_uint * k)(), (ctypes.c_uint * k)()
+    k13, k26, k39 = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_int * k)()
     frac = (ctypes.c_float * k)()
-    nmod = _load().gbhe_crt_tables(p, W, M, k18, k36, bm, frac)
+    nmod = _load().gbhe_crt_tables(p, W, M, k13, k26, k39, frac)
     if nmod != k:
         raise RuntimeError("unexpected number of moduli %d" % nmod)
 
@@ -435,7 +435,7 @@ def crt_tables():
         return sum(int(x) << (32 * i) for i, x in enumerate(words))
 
     return {"p": list(p), "W": [join(W[4 * l:4 * l + 4]) for l in range(k)], "M": join(M[:]),
-            "k18": list(k18), "k36": list(k36), "bm": list(bm), "frac": list(frac)}
+            "k13": list(k13), "k26": list(k26), "k39": list(k39), "frac": list(frac)}
 
 
 def wait_selftest(device=None):

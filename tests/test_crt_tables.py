@@ -2,9 +2,9 @@
 library copies them to the device (host-only, no GPU): the moduli are
 pairwise coprime and small enough for exact FP16 residues and exact FP32
 chunk sums, their product leaves the margin the reconstruction relies on, the
-CRT weights form the idempotent basis, the limb weights and Barrett
-constants are what their definitions say, and reconstruction from residues
-returns every integer in the engine's range."""
+CRT weights form the idempotent basis, the limb weights are what their
+definition says, the FP32 residue split is exact over the operand range, and
+reconstruction from residues returns every integer in the engine's range."""
 import math
 import random
 
@@ -52,18 +52,15 @@ def test_crt_basis(T):
             assert Wl % pj == (1 if j == l else 0), (l, j)
 
 
-def test_limb_weights_and_barrett(T):
-    for pl, k18, k36, bm in zip(T["p"], T["k18"], T["k36"], T["bm"]):
-        assert k18 == pow(2, 18, pl) and k36 == pow(2, 36, pl)
-        assert bm == (1 << 32) // pl
-    # the Barrett quotient of a 32-bit x is floor(x / p) or one less
-    rng = np.random.default_rng(0)
-    xs = np.concatenate([rng.integers(0, 1 << 32, 20000, dtype=np.uint64),
-                         np.array([0, 1, (1 << 32) - 1], dtype=np.uint64)])
-    for pl, bm in zip(T["p"], T["bm"]):
-        q = (xs * np.uint64(bm)) >> np.uint64(32)
-        r = xs - q * np.uint64(pl)
-        assert np.all(r < np.uint64(2 * pl))
+def _sym(x, p):
+    r = x % p
+    return r - p if r > p // 2 else r
+
+
+def test_limb_weights(T):
+    for pl, k13, k26, k39 in zip(T["p"], T["k13"], T["k26"], T["k39"]):
+        assert (k13, k26, k39) == (_sym(1 << 13, pl), _sym(1 << 26, pl), _sym(1 << 39, pl))
+        assert max(abs(k13), abs(k26), abs(k39)) <= 128
 
 
 def test_reconstruction_roundtrip(T):
@@ -115,30 +112,33 @@ def test_quotient_estimate_and_160bit_reconstruction(T):
 
 
 def test_residue_split_replay(T):
-    """The device's residue of a scaled integer |v| <= 2^52: three 18-bit
-    limbs (a, b, c), t = a (2^36 mod p) + b (2^18 mod p) + c, one Barrett
-    step with floor(2^32 / p) and one conditional subtraction, symmetric
-    representative, sign applied.  t stays below 2^32 (no 32-bit overflow),
-    and the result is v mod p with |r| <= 128."""
+    """The device's residue of a scaled integer |v| <= 2^52: four signed
+    13-bit limbs l_i (the sign of v on each), t = l0 + l1 w1 + l2 w2 + l3 w3
+    by an FP32 fma chain with the symmetric limb weights w_i, then
+    r = fmaf(-rintf(t * pinv), p, t) with pinv = 1/p rounded to float.  Every
+    partial sum of t is an integer below 2^23 (so the fma chain is exact, and
+    so is the final fma, whose result is an integer), the only rounding is
+    t * pinv; the replay checks that r = v mod p with |r| <= 128 (exact in
+    FP16, and within the bound of the FP32 chunk sums)."""
     rng = np.random.default_rng(3)
     top = 1 << 52
     # largest magnitude that the rounding to 52 bits can produce: (2^53 - 1 + 1) >> 1
     assert ((1 << 53) - 1 + 1) >> 1 == top
-    mags = [0, 1, top, top - 1, (1 << 36) - 1, 1 << 36, (1 << 18) - 1] + \
-        [int(x) for x in rng.integers(0, top, 5000, dtype=np.int64)]
-    for pl, k18, k36, bm in zip(T["p"], T["k18"], T["k36"], T["bm"]):
-        for mag in mags:
-            a, b, c = mag >> 36, (mag >> 18) & 0x3FFFF, mag & 0x3FFFF
-            t = a * k36 + b * k18 + c
-            assert t < 1 << 32
-            rr = t - ((t * bm) >> 32) * pl
-            assert 0 <= rr < 2 * pl
-            if rr >= pl:
-                rr -= pl
-            sv = rr - pl if rr > pl // 2 else rr
-            assert abs(sv) <= 128
-            for sign in (1, -1):
-                assert (sign * sv - sign * mag) % pl == 0
+    mags = np.array([0, 1, top, top - 1, (1 << 39) - 1, 1 << 39, (1 << 26) - 1, (1 << 13) - 1] +
+                    [int(x) for x in rng.integers(0, top, 20000, dtype=np.int64)], dtype=np.int64)
+    limbs = [(mags >> (13 * i)) & 0x1FFF for i in range(3)] + [mags >> 39]
+    assert int(limbs[3].max()) <= 1 << 13
+    for pl, k13, k26, k39 in zip(T["p"], T["k13"], T["k26"], T["k39"]):
+        pinv = np.float32(1.0) / np.float32(pl)
+        for sign in (1, -1):
+            l0, l1, l2, l3 = (sign * x for x in limbs)
+            t = l0 + l1 * k13 + l2 * k26 + l3 * k39       # exact integers (int64)
+            for part in (l0 + l1 * k13, l0 + l1 * k13 + l2 * k26, t):
+                assert int(np.abs(part).max()) < 1 << 23
+            q = np.rint(t.astype(np.float32) * pinv).astype(np.int64)   # one float32 rounding, half to even
+            r = t - q * pl
+            assert int(np.abs(r).max()) <= 128
+            assert np.all((r - sign * mags) % pl == 0)
 
 
 def _int160_to_double(C, sc):
