@@ -1198,8 +1198,15 @@ size_t crt_budget_bytes(int n, int block) {
 
 int gemm(Ctx& c, const GemmArgs& g, int cplx) {
   if (g.m <= 0 || g.n <= 0) return 0;
+  // The FP64 tensor pipe delivers about 7 GFLOP/s per SM, so a DMMA product
+  // that covers only a few 64 x 64 output tiles runs for hundreds of
+  // microseconds; the tensor-core engine costs a few short launches instead.
+  // Engine products for everything with k >= 16 except products so small
+  // that each DMMA tile holds less than ~5e4 multiply-adds.
   const double work = (double)g.m * g.n * std::max(g.k, 0);
-  const bool use_crt = c.engine == GBHE_ENGINE_CRT && c.crt_ws != nullptr && g.k >= 16 && work >= 2.0e6;
+  const double tiles = std::ceil(g.m / 64.0) * std::ceil(g.n / 64.0);
+  const bool use_crt = c.engine == GBHE_ENGINE_CRT && c.crt_ws != nullptr && g.k >= 16 &&
+                       (work >= 2.0e6 || work > 5.0e4 * std::min(tiles, 152.0));
   if (!use_crt) return cplx ? zgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes)
                             : dgemm(c.st, g, c.gemm_scratch, c.gemm_scratch_bytes);
   // blocks of at most CRT_BLOCK in every dimension; K blocks accumulate in C
