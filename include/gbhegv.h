@@ -227,8 +227,10 @@ int gbhe_hegv_adjoint(gbhe_handle h, int n, int il, int iu, const double* w_all,
 
 /* The complex GEMM that every level-3 step above uses, through the engine
  * selected on the handle (gbhe_set_gemm_engine: the tensor-core CRT GEMM for
- * large products, cut into blocks of gbhe_set_crt_block, and the FP64 DMMA
- * GEMM for small ones), exposed for testing and profiling:
+ * every product with k >= 16 except the tiniest -- those whose DMMA grid
+ * would hold fewer than about 5e4 multiply-adds per 64 x 64 tile -- cut into
+ * blocks of gbhe_set_crt_block, and the FP64 DMMA GEMM for the rest),
+ * exposed for testing and profiling:
  * C = alpha op(A) op(B) + beta C, complex128 column-major.  opA in {0: N,
  * 1: T, 2: C (conjugate transpose), 3: Hermitian matrix read from its lower
  * triangle}; opB in {0: N, 1: T, 2: C}.  lower != 0 writes only C(i,j) with
@@ -240,8 +242,14 @@ int gbhe_zgemm(gbhe_handle h, int opA, int opB, int m, int n, int k, gbhe_cplx a
 
 /* The same product computed on the FP16 tensor cores with exact modular
  * arithmetic (16 moduli <= 256, Chinese remainder reconstruction, one final
- * rounding to double): as accurate as an FP64 GEMM for operands whose
- * rows/columns are not strongly graded.  Complex (cplx != 0, gbhe_cplx
+ * rounding to double).  Each row of op(A) and column of op(B) is rounded to
+ * 53-bit integers relative to its largest entry, and the products of those
+ * integers are exact, so the error is normwise per row and column:
+ *   |err_ij| <= 4 eps (max_k |a_ik| sum_k |b_kj| + sum_k |a_ik| max_k |b_kj|)
+ *               + eps |c_ij|   (complex; independent of k),
+ * which matches an FP64 GEMM for rows/columns of even magnitude and is weaker
+ * than its componentwise bound for entries far below their row/column
+ * maximum.  Complex (cplx != 0, gbhe_cplx
  * operands) or real (cplx = 0, double operands).  opA in {0,1,2,3} as for
  * gbhe_zgemm, opB in {0,1,2}; k <= 65536.  Needs gbhe_crt_workspace_size bytes
  * of workspace beyond the common part (see gbhe_workspace_size); returns
