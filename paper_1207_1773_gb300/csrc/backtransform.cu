@@ -253,32 +253,50 @@ __global__ void __launch_bounds__(256) k_q2_merge(int n, int nb, int J, const cp
   }
 }
 
+// First column that a merged block of pair c can find nonzero when the blocks
+// are applied, in wavefront order, to the identity: every block applied
+// before it mixes only rows >= 2c nb + 1 with each other, and those rows of
+// the identity are zero left of that column.
+__host__ __device__ inline int q2_first_col(int c, int nb) { return 2 * c * nb + 1; }
+
 // Descriptors of merged wavefront step w for the batched products
-//   Wt_z = X[r0 : r0+Wh, c0 : c0+mc]^H V_z          (GEMM 1, mc x 2nb: W_z^H)
-//   X[r0 : r0+Wh, c0 : c0+mc] -= U_z Wt_z^H         (GEMM 2)
-// GEMM 1 is formed transposed so that its long dimension (the columns of X)
-// is the row dimension of the product.
+//   Wt_z = X[r0 : r0+Wh, lo : c0+mc]^H V_z          (GEMM 1, W_z^H)
+//   X[r0 : r0+Wh, lo : c0+mc] -= U_z Wt_z^H         (GEMM 2)
+// with lo = c0, or, when Q2 itself is being formed (X starts as the
+// identity), lo = max(c0, first column the block can reach).  GEMM 1 is
+// formed transposed so that its long dimension (the columns of X) is the row
+// dimension of the product.
 __global__ void k_q2_desc(int n, int nb, int J, int w, int c_lo, int cnt, const cplx* Vm, const cplx* Um, cplx* X,
-                          int ldx, int c0, int mc, cplx* Wbuf, CrtDesc* D1, CrtDesc* D2) {
+                          int ldx, int c0, int mc, int form_q, cplx* Wbuf, CrtDesc* D1, CrtDesc* D2) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= cnt) return;
   const int C = (J + 1) / 2;
   const int c = c_lo + z, j = w - (C - 1 - c);
   const long mid = q2m_mid(c, j, J);
   const int r0 = (2 * c + j) * nb + 1, Wh = min(3 * nb - 1, n - r0), W3 = 3 * nb, NB2 = 2 * nb;
-  cplx* Wz = Wbuf + (size_t)z * NB2 * mc;  // mc x 2nb, ld mc
+  const int lo = form_q ? max(c0, q2_first_col(c, nb)) : c0;
+  const int cols = max(0, c0 + mc - lo);
+  cplx* Wz = Wbuf + (size_t)z * NB2 * mc + (lo - c0);  // cols x 2nb, ld mc
   CrtDesc d;
   d.cmap = nullptr;
-  d.A = X + (size_t)r0 + (size_t)c0 * ldx; d.lda = ldx;  // op C: X window^H
+  d.A = X + (size_t)r0 + (size_t)lo * ldx; d.lda = ldx;  // op C: X window^H
   d.B = Vm + (size_t)mid * W3 * NB2; d.ldb = W3;         // op N
   d.C = Wz; d.ldc = mc;
-  d.M = mc; d.N = NB2; d.K = Wh;
+  d.M = cols; d.N = NB2; d.K = Wh;
   D1[z] = d;
   d.A = Um + (size_t)mid * W3 * NB2; d.lda = W3;         // op N
   d.B = Wz; d.ldb = mc;                                   // op C: Wt^H = W
-  d.C = X + (size_t)r0 + (size_t)c0 * ldx; d.ldc = ldx;
-  d.M = Wh; d.N = mc; d.K = NB2;
+  d.C = X + (size_t)r0 + (size_t)lo * ldx; d.ldc = ldx;
+  d.M = Wh; d.N = cols; d.K = NB2;
   D2[z] = d;
+}
+
+__global__ void k_eye(cplx* Q, int n, int ldq) {
+  const size_t total = (size_t)n * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % n), c = (int)(i / n);
+    Q[(size_t)r + (size_t)c * ldq] = mk(r == c ? 1.0 : 0.0, 0.0);
+  }
 }
 
 // Explicit V of panel p (mp x kr, ld ldv): unit diagonal, zeros above, the
@@ -340,16 +358,30 @@ size_t q2_block_bytes(int n, int nb, int m) {
 
 }  // namespace
 
+// Q2 is formed explicitly (the blocks applied to the identity, each only to
+// the columns it can reach: about 2/3 of the work of applying them to n
+// columns) and then applied as one n x n x m product when at least 4/5 of
+// the eigenvectors are wanted; below that, the blocks go straight to X.
+inline bool q2_form_explicit(int n, int m) { return 5 * (long)m >= 4 * (long)n; }
+
 size_t unmtr_ws_bytes(int n, int nb, int m) {
   const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max(m, 1);
   size_t b = 2 * nn * nb * sizeof(cplx) + 4 * (size_t)nb * mm * sizeof(cplx) + 6 * (size_t)nb * nb * sizeof(cplx) +
              6 * 256;
-  if (nb >= 2 && nb <= 64 && n > 2 * nb) b += q2_block_bytes(n, nb, m);
+  if (nb >= 2 && nb <= 64 && n > 2 * nb) {
+    if (q2_form_explicit(n, m))
+      b += (nn * nn + nn * mm) * sizeof(cplx) + 2 * 256 + q2_block_bytes(n, nb, std::max(n, m));
+    else
+      b += q2_block_bytes(n, nb, m);
+  }
   return b;
 }
 
-// Q2 applied as wavefront-batched merged block reflectors on the tensor-core GEMM.
-static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const cplx* tau2, cplx* X, int ldx) {
+// Q2 applied as wavefront-batched merged block reflectors on the tensor-core
+// GEMM to the m columns of X; with form_q, X is the identity (m = n) and each
+// block touches only the columns it can reach.
+static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const cplx* tau2, cplx* X, int ldx,
+                           bool form_q) {
   Arena& ar = c.arena;
   const size_t save = ar.off;
   const int J = hb2st_J(n, nb);
@@ -395,13 +427,15 @@ static int apply_q2_blocks(Ctx& c, int n, int nb, int m, const cplx* V2, const c
       int c_lo, cnt;
       q2_step_range(J, w, &c_lo, &cnt);
       if (cnt == 0) continue;
-      k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, w, c_lo, cnt, Vm, Um, X, ldx, c0, mcc, Wbuf, D1, D2);
+      k_q2_desc<<<(cnt + 127) / 128, 128, 0, c.st>>>(n, nb, J, w, c_lo, cnt, Vm, Um, X, ldx, c0, mcc, form_q ? 1 : 0,
+                                                      Wbuf, D1, D2);
       count_launch();
-      double gfl = 0.0;  // each of the two products: 8 (2 nb) mcc Wh per merged block
+      double gfl = 0.0;  // each of the two products: 8 (2 nb) cols Wh per merged block
       if (prof_on())
         for (int z = 0; z < cnt; ++z) {
           const int cc = c_lo + z, j = w - (C - 1 - cc);
-          gfl += 8.0 * W2 * mcc * std::min(W3 - 1, n - ((2 * cc + j) * nb + 1));
+          const int lo = form_q ? std::max(c0, q2_first_col(cc, nb)) : c0;
+          gfl += 8.0 * W2 * std::max(0, c0 + mcc - lo) * std::min(W3 - 1, n - ((2 * cc + j) * nb + 1));
         }
       rc = crt_gemm_batched(c.st, OP_C, OP_N, mk(1, 0), mk(0, 0), 1, D1, cnt, mcc, W2, W3 - 1, c.crt_ws,
                             c.crt_ws_bytes, c.status, gfl);
@@ -427,12 +461,33 @@ int unmtr2_run(Ctx& c, int n, int nb, int m, const cplx* A, int lda, const cplx*
   cplx* Ss = ar.take<cplx>((size_t)nb * nb);
   if (!ar.ok() || !Ss) { ar.off = save; return GBHE_EWORKSPACE; }
   const size_t total = (size_t)n * m;
-  k_promote<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, c.st>>>(Z, ldz, n, m, X, ldx);
-  count_launch();
-  GBHE_CUDA(cudaGetLastError());
-  // ---- Q2
-  if (q2_use_blocks(c, n, nb)) {
-    int rc = apply_q2_blocks(c, n, nb, m, V2, tau2, X, ldx);
+  const bool form_q = q2_use_blocks(c, n, nb) && q2_form_explicit(n, m);
+  if (form_q) {
+    // ---- Q2 formed explicitly, then X = Q2 Z in one product
+    cplx* Qe = ar.take<cplx>((size_t)n * n);
+    cplx* Zc = ar.take<cplx>(total);
+    if (!ar.ok() || !Zc) { ar.off = save; return GBHE_EWORKSPACE; }
+    k_eye<<<(int)std::min<size_t>(((size_t)n * n + 255) / 256, 4096), 256, 0, c.st>>>(Qe, n, n);
+    count_launch();
+    k_promote<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, c.st>>>(Z, ldz, n, m, Zc, n);
+    count_launch();
+    GBHE_CUDA(cudaGetLastError());
+    int rc = apply_q2_blocks(c, n, nb, n, V2, tau2, Qe, n, true);
+    if (!rc) {
+      ProfScope prof(c.st, GBHE_PROF_Q2, 0.0, 0.0);
+      rc = zgemm(c, gemm_args(OP_N, OP_N, n, m, n, mk(1, 0), Qe, n, Zc, n, mk(0, 0), X, ldx), nullptr, 0);
+    }
+    if (rc) { ar.off = save; return rc; }
+  } else {
+    k_promote<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, c.st>>>(Z, ldz, n, m, X, ldx);
+    count_launch();
+    GBHE_CUDA(cudaGetLastError());
+  }
+  // ---- Q2 applied to X (unless it was formed above)
+  if (form_q) {
+    // done
+  } else if (q2_use_blocks(c, n, nb)) {
+    int rc = apply_q2_blocks(c, n, nb, m, V2, tau2, X, ldx, false);
     if (rc) { ar.off = save; return rc; }
   } else if (n >= 2) {
     const int J = hb2st_J(n, nb);

@@ -9,13 +9,16 @@
 //      (integer bit manipulation, exact apart from that rounding, which is at
 //      the level of the last bit of the largest element of the row/column).
 //   2. Residues.  The integers are reduced modulo NMOD = 16 pairwise coprime
-//      moduli p_l <= 256 (product M ~ 2^125) to symmetric residues |r| <= 128,
-//      exact in FP16.  Complex operands give two planes (Re, Im) per modulus.
-//      The reduction runs in FP32 on exact integers: four signed 13-bit limbs
-//      of v, t = l0 + l1 w1 + l2 w2 + l3 w3 with w_i the symmetric residues of
-//      2^(13 i) (|t| < 2^23), r = t - p rint(t / p) (|r| <= p/2 + 1 <= 128).
+//      moduli p_l <= 256 (product M ~ 2^125) to symmetric residues
+//      -128 <= r <= 127, stored as signed bytes (the one even modulus, 256,
+//      takes -128 for its residue 128).  Complex operands give two planes
+//      (Re, Im) per modulus.  The reduction runs in FP32 on exact integers:
+//      four signed 13-bit limbs of v, t = l0 + l1 w1 + l2 w2 + l3 w3 with w_i
+//      the symmetric residues of 2^(13 i) (|t| < 2^23), r = t - p rint(t / p)
+//      (|r| <= p/2 + 1 <= 128).
 //   3. Products.  For each modulus the residue products run on tcgen05.mma
-//      kind::f16 (f16 -> f32 accumulators in tensor memory): real operands
+//      kind::f16 (f16 -> f32 accumulators in tensor memory; the producer
+//      warps widen each staged byte tile to FP16, exactly): real operands
 //      one product, complex operands Re C = Ar Br - Ai Bi and
 //      Im C = Ar Bi + Ai Br (the subtraction by the MMA's negate-A bit).
 //      Every partial sum of at most 2^23 / 128^2 = 512 products of
@@ -33,6 +36,7 @@
 // to double: as accurate as an FP64 GEMM for operands whose rows/columns are
 // not strongly graded.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <cuda_fp16.h>
 #include "internal.cuh"
@@ -180,9 +184,9 @@ __global__ void k_fill_int(int* p, int n, int v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
-// Residue planes: P[(l * ncomp + c) * R * Kp + r * Kp + k] (fp16), symmetric
-// residues of the scaled integer of element (r, k); zero for k >= K.
-__device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e, int Kp, __half* P, int bx, int by) {
+// Residue planes: P[(l * ncomp + c) * R * Kp + r * Kp + k] (signed bytes),
+// symmetric residues of the scaled integer of element (r, k); zero for k >= K.
+__device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e, int Kp, int8_t* P, int bx, int by) {
   __shared__ double2 tile[32][33];
   const int r0 = bx * 32, k0 = by * 32;
   if (r0 >= o.R || k0 >= Kp) return;
@@ -198,7 +202,7 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
   __syncthreads();
   const int ncomp = o.cplx ? 2 : 1;
   const size_t plane = (size_t)o.R * Kp;
-  // each thread: one row, four consecutive k (one 8-byte store per plane)
+  // each thread: one row, four consecutive k (one 4-byte store per plane)
   const int t = ty * 32 + tx, q = t >> 3, kq = (t & 7) * 4;
   const int r = r0 + q, k = k0 + kq;
   if (r >= o.R) return;
@@ -232,25 +236,24 @@ __device__ __forceinline__ void op_residues_tile(const Operand& o, const int* e,
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
       if (part == 1 && !o.cplx) break;
-      __half hv[4];
+      unsigned pk = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         // t = v mod-equivalent, an integer below 2^23 (every partial sum exact)
         const float t = fmaf(lim[u][part][3], w3, fmaf(lim[u][part][2], w2, fmaf(lim[u][part][1], w1,
                                                                                    lim[u][part][0])));
-        hv[u] = __float2half_rn(fmaf(-rintf(t * pinv), p, t));  // symmetric, |r| <= 128: exact in FP16
+        float rv = fmaf(-rintf(t * pinv), p, t);  // symmetric, |r| <= 128
+        if (rv > 127.f) rv -= p;                  // 128 only for p = 256: -128 is the same residue
+        pk |= ((unsigned)(int)rv & 0xFFu) << (8 * u);
       }
-      // Kp is a multiple of 32 and k of 4: the 8-byte store is aligned and in the row
-      __half* dst = P + (size_t)(l * ncomp + part) * plane + (size_t)r * Kp + k;
-      uint2 pk;
-      pk.x = (unsigned)__half_as_ushort(hv[0]) | ((unsigned)__half_as_ushort(hv[1]) << 16);
-      pk.y = (unsigned)__half_as_ushort(hv[2]) | ((unsigned)__half_as_ushort(hv[3]) << 16);
-      *reinterpret_cast<uint2*>(dst) = pk;
+      // Kp is a multiple of 32 and k of 4: the 4-byte store is aligned and in the row
+      int8_t* dst = P + (size_t)(l * ncomp + part) * plane + (size_t)r * Kp + k;
+      *reinterpret_cast<unsigned*>(dst) = pk;
     }
   }
 }
 
-__global__ void k_op_residues(Operand oa, const int* ea, __half* PA, Operand ob, const int* eb, __half* PB, int gA,
+__global__ void k_op_residues(Operand oa, const int* ea, int8_t* PA, Operand ob, const int* eb, int8_t* PB, int gA,
                               int Kp) {
   const bool isA = blockIdx.x < (unsigned)gA;
   op_residues_tile(isA ? oa : ob, isA ? ea : eb, Kp, isA ? PA : PB, isA ? blockIdx.x : blockIdx.x - gA, blockIdx.y);
@@ -282,7 +285,7 @@ __global__ void k_bop_exponents(const CrtDesc* D, int opA, int opB, int cplx, in
 }
 
 __global__ void k_bop_residues(const CrtDesc* D, int opA, int opB, int cplx, int maxM, int maxN, const int* ea,
-                               const int* eb, int Kp, __half* PA, __half* PB, int gA) {
+                               const int* eb, int Kp, int8_t* PA, int8_t* PB, int gA) {
   const bool isA = blockIdx.x < (unsigned)gA;
   const Operand o = desc_operand(D[blockIdx.z], isA ? 1 : 0, isA ? opA : opB, cplx);
   const int maxR = isA ? maxM : maxN;
@@ -334,19 +337,94 @@ constexpr int UBM = 128, UBN = 128, UBK = 32;
 constexpr int UTHREADS = 256;
 constexpr int U_APL = UBM * UBK * 2;  // bytes of one plane tile of op(A)
 static_assert(UBM == CBM && UBN == 2 * CBN, "a wide CTA tile covers two tiles of the residue layout");
+// Operands travel as signed bytes (half the bytes of FP16 through L2 and
+// HBM): each K tile is copied by cp.async into a byte staging slot, and the
+// thread that copied a 16-byte chunk widens it to FP16 into the stage the
+// tensor cores read (so no barrier is needed between copy and widening).
 template <bool CPLX, int BN>
 struct UCfg {
   static_assert(BN == UBN || BN == CBN, "tile width 128 or 64");
   static constexpr int NC = CPLX ? 2 : 1;         // planes per operand = accumulators
-  static constexpr int STAGES = CPLX ? 5 : 6;
+  static constexpr int F = 3;                     // FP16 stages read by the tensor cores
+  static constexpr int S8 = 5;                    // byte staging slots (copies run S8 - 1 K tiles ahead)
   static constexpr int KC_TERMS = CPLX ? 256 : 512;  // exact chunk (contraction terms)
   static constexpr int BPL = BN * UBK * 2;           // bytes of one plane tile of op(B)
   static constexpr unsigned BUFC = NC * BN;          // TMEM columns of one buffer
   static constexpr unsigned COLS = 2 * BUFC;         // allocation (two buffers; a power of 2 >= 32)
   static constexpr int NRES = BN / 2;                // columns per epilogue thread
-  static constexpr int STB = NC * (U_APL + BPL);     // bytes per pipeline stage
-  static constexpr size_t SMEM = (size_t)STAGES * STB + (size_t)NC * BN * OPITCH + 8 * (STAGES + 3) + 16;
+  static constexpr int STB = NC * (U_APL + BPL);     // bytes per FP16 stage
+  static constexpr int ST8 = NC * (UBM + BN) * UBK;  // bytes per byte staging slot
+  static constexpr int NCH_A = NC * UBM * 2;         // 16-byte chunks of op(A) per K tile (two per row)
+  static constexpr int NCH = NC * (UBM + BN) * 2;    // 16-byte chunks per K tile
+  static constexpr size_t SMEM =
+      (size_t)F * STB + (size_t)S8 * ST8 + (size_t)NC * BN * OPITCH + 8 * (F + 3) + 16;
 };
+
+// Two signed bytes of `ub` (already biased by +128 per byte), selected by
+// `sel`, to an FP16 pair: the byte placed under the exponent bits of 1024
+// (0x64uu = 1024 + u) minus 1152 gives u - 128 exactly.
+__device__ __forceinline__ unsigned h2_of_bytes(unsigned ub, unsigned sel) {
+  unsigned out;
+  asm("{\n\t.reg .b32 t;\n\tprmt.b32 t, %1, %2, %3;\n\tsub.rn.f16x2 %0, t, %4;\n\t}"
+      : "=r"(out)
+      : "r"(ub), "r"(0x64646464u), "r"(sel), "r"(0x64806480u));
+  return out;
+}
+// 16 signed bytes (contraction index k .. k+15 of one row) to the two FP16
+// core-matrix rows k .. k+7 (lo) and k+8 .. k+15 (hi).
+__device__ __forceinline__ void widen16(const uint4 v, uint4& lo, uint4& hi) {
+  const unsigned a = v.x ^ 0x80808080u, b = v.y ^ 0x80808080u, c = v.z ^ 0x80808080u, d = v.w ^ 0x80808080u;
+  lo = make_uint4(h2_of_bytes(a, 0x4140u), h2_of_bytes(a, 0x4342u), h2_of_bytes(b, 0x4140u), h2_of_bytes(b, 0x4342u));
+  hi = make_uint4(h2_of_bytes(c, 0x4140u), h2_of_bytes(c, 0x4342u), h2_of_bytes(d, 0x4140u), h2_of_bytes(d, 0x4342u));
+}
+
+// Copy (issue) and widening of K tile `it` by the `nthr` threads t = 0 ..
+// nthr - 1 of a CTA: chunk i < NCH_A is row r = (i % (2 UBM)) / 2, half hk =
+// i % 2 of plane c = i / (2 UBM) of op(A); the rest likewise of op(B).  Rows
+// beyond the matrix are zero-filled by the copy (source size 0).
+template <bool CPLX, int BN, int NTHR>
+__device__ __forceinline__ void stage_issue(unsigned char* s8, const int8_t* PA, const int8_t* PB, size_t planeA,
+                                            size_t planeB, int l, int k0, int Kp, int m0, int n0, int M, int N,
+                                            int t) {
+  using CF = UCfg<CPLX, BN>;
+  const int8_t* Al = PA + (size_t)l * CF::NC * planeA;
+  const int8_t* Bl = PB + (size_t)l * CF::NC * planeB;
+#pragma unroll
+  for (int i = t; i < CF::NCH_A; i += NTHR) {
+    const int c = i / (UBM * 2), rem = i % (UBM * 2), r = rem >> 1, hk = rem & 1;
+    const bool ok = (m0 + r) < M;
+    cp16(s8 + i * 16, Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + hk * 16, ok);
+  }
+#pragma unroll
+  for (int i = CF::NCH_A + t; i < CF::NCH; i += NTHR) {
+    const int j = i - CF::NCH_A, c = j / (BN * 2), rem = j % (BN * 2), r = rem >> 1, hk = rem & 1;
+    const bool ok = (n0 + r) < N;
+    cp16(s8 + i * 16, Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + hk * 16, ok);
+  }
+}
+template <bool CPLX, int BN, int NTHR>
+__device__ __forceinline__ void stage_widen(const unsigned char* s8, unsigned char* sA, int t) {
+  using CF = UCfg<CPLX, BN>;
+  unsigned char* sB = sA + CF::NC * U_APL;
+#pragma unroll
+  for (int i = t; i < CF::NCH_A; i += NTHR) {
+    const int c = i / (UBM * 2), rem = i % (UBM * 2), r = rem >> 1, hk = rem & 1;
+    uint4 lo, hi;
+    widen16(*reinterpret_cast<const uint4*>(s8 + i * 16), lo, hi);
+    unsigned char* d = sA + c * U_APL + ((r >> 3) * 4 + 2 * hk) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(d) = lo;
+    *reinterpret_cast<uint4*>(d + 128) = hi;
+  }
+#pragma unroll
+  for (int i = CF::NCH_A + t; i < CF::NCH; i += NTHR) {
+    const int j = i - CF::NCH_A, c = j / (BN * 2), rem = j % (BN * 2), r = rem >> 1, hk = rem & 1;
+    uint4 lo, hi;
+    widen16(*reinterpret_cast<const uint4*>(s8 + i * 16), lo, hi);
+    unsigned char* d = sB + c * CF::BPL + ((r >> 3) * 4 + 2 * hk) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(d) = lo;
+    *reinterpret_cast<uint4*>(d + 128) = hi;
+  }
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -410,18 +488,19 @@ __device__ __forceinline__ void tmem_ld16(unsigned addr, float (&v)[16]) {
 // several exact chunks (Kp > KC_TERMS); single-chunk products use
 // k_crt_umma_ws below.
 template <bool CPLX, int BN>
-__global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, const __half* PB, int M, int N, int Kp,
+__global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const int8_t* PA, const int8_t* PB, int M, int N, int Kp,
                                                          unsigned char* Out, const CrtDesc* D, int maxM, int maxN,
                                                          int lower, int mpc, int* status) {
   using CF = UCfg<CPLX, BN>;
   constexpr int NC = CF::NC;
-  constexpr int STAGES = CF::STAGES;
+  constexpr int F = CF::F, S8 = CF::S8, LAG = S8 - 1;
   constexpr int STB = CF::STB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* stile = smem_raw + STAGES * STB;
-  // bars: [0, STAGES) stage empty, STAGES + b accumulator b full, STAGES + 2 drain (before TMEM is freed)
+  unsigned char* stage8 = smem_raw + F * STB;
+  unsigned char* stile = stage8 + S8 * CF::ST8;
+  // bars: [0, F) FP16 stage empty, F + b accumulator b full, F + 2 drain (before TMEM is freed)
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(stile + NC * BN * OPITCH);
-  unsigned* tslot = reinterpret_cast<unsigned*>(bars + STAGES + 3);
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + F + 3);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + BN - 1) / BN;
@@ -452,7 +531,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   const size_t planeA = (size_t)M * Kp, planeB = (size_t)N * Kp;
 
   if (t == 0) {
-    for (int i = 0; i < STAGES + 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
+    for (int i = 0; i < F + 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sabort = 0;
   }
@@ -474,26 +553,13 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   const unsigned idesc = (1u << 4) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
   const unsigned idesc_negA = idesc | (1u << 13);
 
-  auto load = [&](int it) {
-    unsigned char* sA = smem_raw + (it % STAGES) * STB;
-    unsigned char* sB = sA + NC * U_APL;
-    const int l = l0 + it / ktiles, k0 = (it % ktiles) * UBK;
-    const __half* Al = PA + (size_t)l * NC * planeA;
-    const __half* Bl = PB + (size_t)l * NC * planeB;
-#pragma unroll
-    for (int i = t; i < NC * UBM * 4; i += UTHREADS) {
-      const int c = i / (UBM * 4), rem = i % (UBM * 4), r = rem >> 2, kg = rem & 3;
-      const bool ok = (m0 + r) < M;
-      const __half* src = Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + kg * 8;
-      cp16(sA + c * U_APL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
-    }
-#pragma unroll
-    for (int i = t; i < NC * BN * 4; i += UTHREADS) {
-      const int c = i / (BN * 4), rem = i % (BN * 4), r = rem >> 2, kg = rem & 3;
-      const bool ok = (n0 + r) < N;
-      const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + kg * 8;
-      cp16(sB + c * CF::BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
-    }
+  // copies of K tile `it` into its byte slot; widening into its FP16 stage
+  auto issue = [&](int it) {
+    stage_issue<CPLX, BN, UTHREADS>(stage8 + (it % S8) * CF::ST8, PA, PB, planeA, planeB, l0 + it / ktiles,
+                                    (it % ktiles) * UBK, Kp, m0, n0, M, N, t);
+  };
+  auto widen = [&](int it) {
+    stage_widen<CPLX, BN, UTHREADS>(stage8 + (it % S8) * CF::ST8, smem_raw + (it % F) * STB, t);
   };
 
   // running residues of this thread's row (32 q + lane) and NRES columns (NRES h + x)
@@ -506,7 +572,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
 
   auto epilogue = [&](int u) {
     const int b = u & 1;
-    if (!mbar_wait(smem_addr(bars + STAGES + b), (unsigned)(u >> 1) & 1u)) {
+    if (!mbar_wait(smem_addr(bars + F + b), (unsigned)(u >> 1) & 1u)) {
       *sabort = 1;
       if (status) set_err_once(status, GBHE_ETIMEOUT);
     }
@@ -551,18 +617,23 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     }
   };
 
-#pragma unroll
-  for (int s = 0; s < STAGES - 1; ++s) {
-    if (s < iters) load(s);
+  for (int s = 0; s < LAG; ++s) {
+    if (s < iters) issue(s);
     cp_commit();
   }
   bool aborted = false;
   for (int it = 0; it < iters; ++it) {
-    const int s = it % STAGES;
+    const int f = it % F;
     const int kt = it % ktiles;
     const int u = (it / ktiles) * nch + kt / KTC;
     const bool unit_start = (kt % KTC) == 0;
-    cp_wait<STAGES - 2>();
+    cp_wait<LAG - 1>();  // this thread's copies of K tile `it` have landed
+    // FP16 stage f is free once the products of K tile it - F have completed
+    if (it >= F && !mbar_wait(smem_addr(bars + f), (unsigned)((it / F) - 1) & 1u)) {
+      *sabort = 1;
+      if (status) set_err_once(status, GBHE_ETIMEOUT);
+    }
+    widen(it);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     // one decision for the whole CTA: a timeout recorded by any thread before
     // this barrier stops every thread at the same iteration
@@ -571,7 +642,7 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
     if (stop) { aborted = true; break; }
     if (t == 0) {
       const unsigned dbuf = tmem + (unsigned)(u & 1) * CF::BUFC;
-      const unsigned sA = smem_addr(smem_raw + s * STB), sB = sA + NC * U_APL;
+      const unsigned sA = smem_addr(smem_raw + f * STB), sB = sA + NC * U_APL;
 #pragma unroll
       for (int kk = 0; kk < UBK / 16; ++kk) {
         const unsigned first = (unit_start && kk == 0) ? 0u : 1u;
@@ -586,17 +657,11 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
           umma_f16(dbuf + BN, ai, br, idesc, 1u);     // Im += Ai Br
         }
       }
-      umma_commit(smem_addr(bars + s));
-      if ((kt % KTC) == KTC - 1 || kt == ktiles - 1) umma_commit(smem_addr(bars + STAGES + (u & 1)));
+      umma_commit(smem_addr(bars + f));
+      if ((kt % KTC) == KTC - 1 || kt == ktiles - 1) umma_commit(smem_addr(bars + F + (u & 1)));
     }
-    // refill the stage read by the previous iteration's products
-    if (it + STAGES - 1 < iters) {
-      if (it >= 1 && !mbar_wait(smem_addr(bars + (it - 1) % STAGES), (unsigned)((it - 1) / STAGES) & 1u)) {
-        *sabort = 1;
-        if (status) set_err_once(status, GBHE_ETIMEOUT);
-      }
-      load(it + STAGES - 1);
-    }
+    // the byte slot of K tile it + LAG is the one this thread widened at it - 1
+    if (it + LAG < iters) issue(it + LAG);
     cp_commit();
     if (unit_start && u > 0) epilogue(u - 1);
   }
@@ -606,8 +671,8 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
   // issuing thread commits once more and waits for that commit (bounded), also
   // on the path that gave up early
   if (t == 0) {
-    umma_commit(smem_addr(bars + STAGES + 2));
-    if (!mbar_wait(smem_addr(bars + STAGES + 2), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
+    umma_commit(smem_addr(bars + F + 2));
+    if (!mbar_wait(smem_addr(bars + F + 2), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -623,14 +688,15 @@ __global__ void __launch_bounds__(UTHREADS, 1) k_crt_umma(const __half* PA, cons
 // 128 producers, each after its own copies of the stage completed and were
 // fenced for the tensor cores) and "empty" (MMA completion), per TMEM buffer
 // "full" (MMA completion) and "drained" (the 256 epilogue threads).  The
-// producers run WS_LAG stages ahead of the stage they report ready, so the
-// MMA warp never waits on the producers' refill of the stage it just read.
+// producers copy byte tiles WS_LAG K tiles ahead of the tile they widen and
+// report ready, so the MMA warp never waits on the copies of the stage it
+// just read.
 // The epilogue stores each residue byte straight from its register to the
 // tile-major output layout (a warp covers 32 consecutive rows of one column:
 // one 32-byte segment per store), so no shared-memory staging tile is needed
 // and the shared memory goes to a deeper operand pipeline.
 // Grid and arguments as for k_crt_umma, 384 threads.
-constexpr int WS_STAGES = 6, WS_LAG = 3;
+constexpr int WS_F = 4, WS_S8 = 4, WS_LAG = WS_S8 - 1;  // FP16 stages, byte slots, copy lead
 constexpr int WS_THREADS = 416, WS_EPI = 256;
 
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
@@ -652,21 +718,24 @@ template <bool CPLX, int BN>
 struct WsCfg {
   static constexpr int NC = UCfg<CPLX, BN>::NC;
   static constexpr int STB = UCfg<CPLX, BN>::STB;
-  static constexpr size_t SMEM = (size_t)WS_STAGES * STB + 8 * (2 * WS_STAGES + 5) + 16;
+  static constexpr int ST8 = UCfg<CPLX, BN>::ST8;
+  static constexpr size_t SMEM = (size_t)WS_F * STB + (size_t)WS_S8 * ST8 + 8 * (2 * WS_F + 5) + 16;
 };
 
 template <bool CPLX, int BN>
-__global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA, const __half* PB, int M, int N,
+__global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const int8_t* PA, const int8_t* PB, int M, int N,
                                                             int Kp, unsigned char* Out, const CrtDesc* D, int maxM,
                                                             int maxN, int lower, int mpc, int* status) {
   using CF = UCfg<CPLX, BN>;
   constexpr int NC = CF::NC;
   constexpr int STB = CF::STB;
+  constexpr int S = WS_F;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + WS_STAGES * STB);
-  // bars: [0, S) stage empty, S + b accumulator full, S + 2 + b accumulator drained,
-  // S + 4 drain of every issued MMA (before TMEM is freed), S + 5 + s stage ready
-  unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2 * WS_STAGES + 5);
+  unsigned char* stage8 = smem_raw + S * STB;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage8 + WS_S8 * CF::ST8);
+  // bars: [0, S) FP16 stage empty, S + b accumulator full, S + 2 + b accumulator drained,
+  // S + 4 drain of every issued MMA (before TMEM is freed), S + 5 + s FP16 stage ready
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2 * S + 5);
   volatile int* sabort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int TM = (maxM + UBM - 1) / UBM, TN2 = (maxN + BN - 1) / BN;
@@ -695,13 +764,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   const size_t planeA = (size_t)M * Kp, planeB = (size_t)N * Kp;
 
   if (t == 0) {
-    for (int i = 0; i < WS_STAGES + 2; ++i)
+    for (int i = 0; i < S + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + i)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + WS_STAGES + 4)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + S + 4)));
     for (int i = 0; i < 2; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + WS_STAGES + 2 + i)), "r"(WS_EPI));
-    for (int i = 0; i < WS_STAGES; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + WS_STAGES + 5 + i)), "r"(128));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + S + 2 + i)), "r"(WS_EPI));
+    for (int i = 0; i < S; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + S + 5 + i)), "r"(128));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sabort = 0;
   }
@@ -718,57 +787,40 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
   const int iters = mpc * ktiles;
 
   if (w < 4) {
-    // ---------------- producers (128 threads)
-    auto load = [&](int it) {
-      unsigned char* sA = smem_raw + (it % WS_STAGES) * STB;
-      unsigned char* sB = sA + NC * U_APL;
-      const int l = l0 + it / ktiles, k0 = (it % ktiles) * UBK;
-      const __half* Al = PA + (size_t)l * NC * planeA;
-      const __half* Bl = PB + (size_t)l * NC * planeB;
-#pragma unroll
-      for (int i = t; i < NC * UBM * 4; i += 128) {
-        const int c = i / (UBM * 4), rem = i % (UBM * 4), r = rem >> 2, kg = rem & 3;
-        const bool ok = (m0 + r) < M;
-        const __half* src = Al + (size_t)c * planeA + (size_t)(ok ? m0 + r : 0) * Kp + k0 + kg * 8;
-        cp16(sA + c * U_APL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
-      }
-#pragma unroll
-      for (int i = t; i < NC * BN * 4; i += 128) {
-        const int c = i / (BN * 4), rem = i % (BN * 4), r = rem >> 2, kg = rem & 3;
-        const bool ok = (n0 + r) < N;
-        const __half* src = Bl + (size_t)c * planeB + (size_t)(ok ? n0 + r : 0) * Kp + k0 + kg * 8;
-        cp16(sB + c * CF::BPL + ((r >> 3) * 4 + kg) * 128 + (r & 7) * 16, src, ok);
-      }
+    // ---------------- producers (128 threads): copy byte tiles, widen them to FP16
+    auto issue = [&](int it) {
+      stage_issue<CPLX, BN, 128>(stage8 + (it % WS_S8) * CF::ST8, PA, PB, planeA, planeB, l0 + it / ktiles,
+                                 (it % ktiles) * UBK, Kp, m0, n0, M, N, t);
     };
-    // my copies of stage `it` are complete: fence them for the tensor cores and report
-    auto ready = [&](int it) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_addr(bars + WS_STAGES + 5 + it % WS_STAGES));
-    };
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % WS_STAGES;
-      if (it >= WS_STAGES)  // the MMAs of iteration it - S have read the stage
-        mbar_wait_cta(smem_addr(bars + s), (unsigned)((it / WS_STAGES) - 1) & 1u, sabort, status);
-      load(it);
+    for (int it = 0; it < WS_LAG; ++it) {
+      if (it < iters) issue(it);
       cp_commit();
-      if (it >= WS_LAG) {
-        cp_wait<WS_LAG>();  // every group but the newest WS_LAG is complete
-        ready(it - WS_LAG);
-      }
+    }
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % S;
+      // the byte slot of K tile it + WS_LAG is the one this thread widened at it - 1
+      if (it + WS_LAG < iters) issue(it + WS_LAG);
+      cp_commit();
+      cp_wait<WS_LAG>();  // this thread's copies of K tile `it` have landed
+      if (it >= S)        // the MMAs of K tile it - S have read the FP16 stage
+        mbar_wait_cta(smem_addr(bars + s), (unsigned)((it / S) - 1) & 1u, sabort, status);
+      stage_widen<CPLX, BN, 128>(stage8 + (it % WS_S8) * CF::ST8, smem_raw + s * STB, t);
+      // my part of the stage is written: fence it for the tensor cores and report
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_addr(bars + S + 5 + s));
     }
     cp_wait<0>();
-    for (int it = std::max(0, iters - WS_LAG); it < iters; ++it) ready(it);
   } else if (w == 4) {
     // ---------------- MMA issue (one lane of warp 4)
     const unsigned idesc = (1u << 4) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(UBM >> 4) << 24);
     const unsigned idesc_negA = idesc | (1u << 13);
     for (int it = 0; it < iters; ++it) {
-      const int s = it % WS_STAGES;
+      const int s = it % S;
       const int li = it / ktiles, kt = it % ktiles, b = li & 1;
       // buffer b must have been drained by the epilogue of modulus li - 2
       if (kt == 0 && li >= 2)
-        mbar_wait_cta(smem_addr(bars + WS_STAGES + 2 + b), (unsigned)((li - 2) >> 1) & 1u, sabort, status);
-      mbar_wait_cta(smem_addr(bars + WS_STAGES + 5 + s), (unsigned)(it / WS_STAGES) & 1u, sabort, status);
+        mbar_wait_cta(smem_addr(bars + S + 2 + b), (unsigned)((li - 2) >> 1) & 1u, sabort, status);
+      mbar_wait_cta(smem_addr(bars + S + 5 + s), (unsigned)(it / S) & 1u, sabort, status);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (lane == 0) {
         const unsigned dbuf = tmem + (unsigned)b * CF::BUFC;
@@ -788,15 +840,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
           }
         }
         umma_commit(smem_addr(bars + s));
-        if (kt == ktiles - 1) umma_commit(smem_addr(bars + WS_STAGES + b));
+        if (kt == ktiles - 1) umma_commit(smem_addr(bars + S + b));
       }
       __syncwarp();
     }
     // every MMA issued here has completed before TMEM is freed (bounded wait;
     // also when a timeout made the other waits give up)
     if (lane == 0) {
-      umma_commit(smem_addr(bars + WS_STAGES + 4));
-      if (!mbar_wait(smem_addr(bars + WS_STAGES + 4), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
+      umma_commit(smem_addr(bars + S + 4));
+      if (!mbar_wait(smem_addr(bars + S + 4), 0u) && status) set_err_once(status, GBHE_ETIMEOUT);
     }
     __syncwarp();
   } else {
@@ -811,7 +863,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
     for (int li = 0; li < mpc; ++li) {
       const int b = li & 1, l = l0 + li;
       unsigned char* obase = Out + ((size_t)tile * NMOD + l) * NC * OTILE + (size_t)ct0 * CBM + il;
-      mbar_wait_cta(smem_addr(bars + WS_STAGES + b), (unsigned)(li >> 1) & 1u, sabort, status);
+      mbar_wait_cta(smem_addr(bars + S + b), (unsigned)(li >> 1) & 1u, sabort, status);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float p = (float)c_p[l], pinv = c_pinv[l];
       const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * CF::BUFC + (unsigned)(NRES * hh);
@@ -832,7 +884,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_crt_umma_ws(const __half* PA,
           }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(smem_addr(bars + WS_STAGES + 2 + b));  // buffer b may be overwritten
+      mbar_arrive(smem_addr(bars + S + 2 + b));  // buffer b may be overwritten
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1080,7 +1132,7 @@ int umma_prepare(int* nsm_out) {
 }
 
 template <bool CPLX, int BN>
-int launch_umma_bn(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
+int launch_umma_bn(cudaStream_t st, const int8_t* PA, const int8_t* PB, int M, int N, int Kp, unsigned char* Out,
                    const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
   const bool one = Kp <= UCfg<CPLX, BN>::KC_TERMS;
   int nsm = 0;
@@ -1103,7 +1155,7 @@ int launch_umma_bn(cudaStream_t st, const __half* PA, const __half* PB, int M, i
 }
 
 template <bool CPLX>
-int launch_umma(cudaStream_t st, const __half* PA, const __half* PB, int M, int N, int Kp, unsigned char* Out,
+int launch_umma(cudaStream_t st, const int8_t* PA, const int8_t* PB, int M, int N, int Kp, unsigned char* Out,
                 const CrtDesc* D, int maxM, int maxN, int lower, int nbatch, int* status) {
   if (maxN <= CBN)
     return launch_umma_bn<CPLX, CBN>(st, PA, PB, M, N, Kp, Out, D, maxM, maxN, lower, nbatch, status);
@@ -1114,8 +1166,8 @@ size_t crt_bytes(int M, int N, int K, int cplx) {
   const size_t Kp = (size_t)(K + CBK - 1) / CBK * CBK;
   const int nc = cplx ? 2 : 1;
   size_t b = 0;
-  b += (size_t)NMOD * nc * (size_t)M * Kp * 2 + 256;
-  b += (size_t)NMOD * nc * (size_t)N * Kp * 2 + 256;
+  b += (size_t)NMOD * nc * (size_t)M * Kp + 256;
+  b += (size_t)NMOD * nc * (size_t)N * Kp + 256;
   b += out_bytes(M, N, cplx) + 256;
   b += ((size_t)M + N) * sizeof(int) + 256;
   return b;
@@ -1138,8 +1190,8 @@ size_t crt_batched_ws_bytes(int nbatch, int maxM, int maxN, int maxK, int cplx) 
   const int nc = cplx ? 2 : 1;
   const size_t nbt = (size_t)std::max(nbatch, 1);
   size_t b = 0;
-  b += nbt * NMOD * nc * (size_t)maxM * Kp * 2 + 256;
-  b += nbt * NMOD * nc * (size_t)maxN * Kp * 2 + 256;
+  b += nbt * NMOD * nc * (size_t)maxM * Kp + 256;
+  b += nbt * NMOD * nc * (size_t)maxN * Kp + 256;
   b += nbt * out_bytes(maxM, maxN, cplx) + 256;
   b += nbt * ((size_t)maxM + maxN) * sizeof(int) + 256;
   return b;
@@ -1156,8 +1208,8 @@ int crt_gemm_batched(cudaStream_t st, int opA, int opB, cplx alpha, cplx beta, i
   const int nc = cplx_flag ? 2 : 1;
   char* p = reinterpret_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
-  __half* PA = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxM * Kp * 2));
-  __half* PB = reinterpret_cast<__half*>(take((size_t)nbatch * NMOD * nc * maxN * Kp * 2));
+  int8_t* PA = reinterpret_cast<int8_t*>(take((size_t)nbatch * NMOD * nc * maxM * Kp));
+  int8_t* PB = reinterpret_cast<int8_t*>(take((size_t)nbatch * NMOD * nc * maxN * Kp));
   unsigned char* Out = reinterpret_cast<unsigned char*>(take((size_t)nbatch * out_bytes(maxM, maxN, cplx_flag)));
   int* ea = reinterpret_cast<int*>(take((size_t)nbatch * (maxM + maxN) * sizeof(int)));
   int* eb = ea + (size_t)nbatch * maxM;
@@ -1269,8 +1321,8 @@ int crt_gemm(cudaStream_t st, const GemmArgs& g, int cplx, void* ws, size_t ws_b
   if (crt_bytes(M, N, K, cplx) > ws_bytes) return GBHE_EWORKSPACE;
   char* p = reinterpret_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~size_t(255); return q; };
-  __half* PA = reinterpret_cast<__half*>(take((size_t)NMOD * nc * M * Kp * 2));
-  __half* PB = reinterpret_cast<__half*>(take((size_t)NMOD * nc * N * Kp * 2));
+  int8_t* PA = reinterpret_cast<int8_t*>(take((size_t)NMOD * nc * M * Kp));
+  int8_t* PB = reinterpret_cast<int8_t*>(take((size_t)NMOD * nc * N * Kp));
   unsigned char* Out = reinterpret_cast<unsigned char*>(take(out_bytes(M, N, cplx)));
   int* ea = reinterpret_cast<int*>(take((size_t)(M + N) * sizeof(int)));
   int* eb = ea + M;

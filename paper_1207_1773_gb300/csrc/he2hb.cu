@@ -5,7 +5,7 @@
 // For each panel (columns k..k+nb-1):
 //   (a) QR of the panel P = A[k+nb:n, k:k+nb] = Q R,  Q = I - V T V^H
 //       (one cooperative kernel: rows split over the CTAs, each CTA keeps its
-//       rows in shared memory; two bounded grid barriers per column);
+//       rows in shared memory; one bounded grid barrier per column);
 //   (c) two-sided update of the trailing matrix A22 <- Q^H A22 Q as
 //       X = A22 V T,  W = X - 1/2 V (T^H V^H X),  A22 -= V W^H + W V^H
 //       (A22 read as Hermitian from its lower triangle and only the lower
@@ -35,8 +35,8 @@ struct PanelArgs {
   int ldv;
   cplx* tau;   // tau1 + k
   cplx* T;     // nb x nb, ld nb
-  cplx* part;  // G x (nb + 1) partial sums
-  cplx* alpha; // 1 slot
+  cplx* part;  // 2 x G x (nb + 1) partial sums (double-buffered by column parity)
+  cplx* row;   // 2 x nb: the pivot row of the next column (double-buffered)
   unsigned* bar;
   int* st;
 };
@@ -50,10 +50,22 @@ __device__ __forceinline__ cplx warp_sum(cplx v) {
   return v;
 }
 
+// Householder QR of the panel with one grid barrier per column.  The
+// reflector of column j is v = (x - beta e_j) / (alpha - beta) (x the column,
+// alpha = x_j), so everything the update needs can be summed over the CTAs
+// from the UNSCALED column in one round:
+//   |x(j+1:)|^2,  x^H P(:, c) (c > j),  V(:, c)^H x (c < j; for T),
+// plus the pivot row P(j, :) published by its owner; then
+//   w_c = v^H P(:, c) = conj(s) (x^H P(:, c) - beta P(j, c)),
+//   V(:, c)^H v = s (V(:, c)^H x - beta conj(V(j, c))),  s = 1 / (alpha - beta),
+// and after the update each CTA forms its parts of the next column's sums
+// before the barrier.  Partial sums and the pivot row alternate between two
+// buffers, so a CTA that runs ahead never overwrites what a slower one still
+// reads (it cannot pass the next barrier before the slower one arrives).
 __global__ void __launch_bounds__(PT) k_panel_qr(PanelArgs p) {
   extern __shared__ cplx S[];  // chunk x nb, ld chunk
-  __shared__ cplx wtot[128];
-  __shared__ cplx red[PT / 32];
+  __shared__ cplx wsum[128], cw[128], vv[128];
+  __shared__ double rednrm[PT / 32];
   __shared__ cplx sh_tau, sh_scal;
   __shared__ double sh_beta;
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -67,92 +79,107 @@ __global__ void __launch_bounds__(PT) k_panel_qr(PanelArgs p) {
     for (int i = t; i < nb * nb; i += PT) p.T[i] = mk(0.0, 0.0);
   __syncthreads();
 
-  for (int j = 0; j < p.kr; ++j) {
-    // ---- phase 1: partial |x|^2 below the diagonal of column j
+  // this CTA's parts of the sums of column j (rows gi >= j) into buffer j & 1,
+  // and the pivot row j if this CTA holds it
+  auto sums = [&](int j) {
+    cplx* pb = p.part + ((size_t)(j & 1) * G + b) * PS;
     double s = 0.0;
-    for (int r = t; r < rows; r += PT) {
-      int gi = r0 + r;
-      if (gi > j) s += cabs2(S[r + j * p.chunk]);
+    for (int r = t; r < rows; r += PT)
+      if (r0 + r > j) s += cabs2(S[r + j * p.chunk]);
+    s = warp_sum(mk(s, 0.0)).x;
+    if (lane == 0) rednrm[warp] = s;
+    for (int c = warp; c < nb; c += PT / 32) {
+      if (c == j) continue;
+      cplx acc = mk(0.0, 0.0);
+      for (int r = lane; r < rows; r += 32) {
+        if (r0 + r < j) continue;
+        const cplx x = S[r + j * p.chunk];
+        if (c > j) ccfma(acc, x, S[r + c * p.chunk]);  // conj(x_i) P(i, c)
+        else ccfma(acc, S[r + c * p.chunk], x);        // conj(V(i, c)) x_i
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) pb[1 + c] = acc;
     }
-    cplx sv = warp_sum(mk(s, 0.0));
-    if (lane == 0) red[warp] = sv;
+    if (j >= r0 && j < r1) {
+      cplx* rw = p.row + (size_t)(j & 1) * nb;
+      for (int c = t; c < nb; c += PT) rw[c] = S[(j - r0) + c * p.chunk];
+    }
     __syncthreads();
     if (t == 0) {
       double tot = 0.0;
-      for (int w = 0; w < PT / 32; ++w) tot += red[w].x;
-      p.part[(size_t)b * PS] = mk(tot, 0.0);
-      if (j >= r0 && j < r1) *p.alpha = S[(j - r0) + j * p.chunk];
+      for (int w = 0; w < PT / 32; ++w) tot += rednrm[w];
+      pb[0] = mk(tot, 0.0);
     }
+  };
+
+  if (p.kr > 0) sums(0);
+  for (int j = 0; j < p.kr; ++j) {
     if (!grid_barrier(p.bar, G, p.st)) return;
-    // ---- phase 2: reflector, scale v, partial sums of V^H v_j and v_j^H P
+    const cplx* pbuf = p.part + (size_t)(j & 1) * G * PS;
+    const cplx* rw = p.row + (size_t)(j & 1) * nb;
+    // ---- totals over the CTAs
     if (warp == 0) {
       double x2 = 0.0;
-      for (int q = lane; q < G; q += 32) x2 += __ldcg(&p.part[(size_t)q * PS]).x;
-      cplx tt = warp_sum(mk(x2, 0.0));
+      for (int q = lane; q < G; q += 32) x2 += __ldcg(&pbuf[(size_t)q * PS]).x;
+      x2 = warp_sum(mk(x2, 0.0)).x;
       if (lane == 0) {
-        cplx al = __ldcg(p.alpha);
-        double xn2 = tt.x;
-        if (xn2 == 0.0 && al.y == 0.0) {
+        const cplx al = __ldcg(&rw[j]);
+        if (x2 == 0.0 && al.y == 0.0) {
           sh_tau = mk(0.0, 0.0); sh_beta = al.x; sh_scal = mk(0.0, 0.0);
         } else {
-          double nrm = sqrt(al.x * al.x + al.y * al.y + xn2);
-          double beta = (al.x >= 0.0) ? -nrm : nrm;
+          const double nrm = sqrt(al.x * al.x + al.y * al.y + x2);
+          const double beta = (al.x >= 0.0) ? -nrm : nrm;
           sh_beta = beta;
           sh_tau = mk((beta - al.x) / beta, -al.y / beta);
           sh_scal = cinv(mk(al.x - beta, al.y));
         }
       }
     }
-    __syncthreads();
-    const cplx tau = sh_tau, scal = sh_scal;
-    for (int r = t; r < rows; r += PT) {
-      int gi = r0 + r;
-      if (gi > j) S[r + j * p.chunk] = cmul(S[r + j * p.chunk], scal);
-      else if (gi == j) S[r + j * p.chunk] = mk(sh_beta, 0.0);
-    }
-    if (b == 0 && t == 0) p.tau[j] = tau;
-    __syncthreads();
-    for (int c = warp; c < nb; c += PT / 32) {
-      if (c == j) continue;
-      cplx acc = mk(0.0, 0.0);
-      for (int r = lane; r < rows; r += 32) {
-        int gi = r0 + r;
-        if (gi < j) continue;
-        cplx vj = (gi == j) ? mk(1.0, 0.0) : S[r + j * p.chunk];
-        if (c < j) ccfma(acc, S[r + c * p.chunk], vj);      // conj(V(i,c)) v_j(i)
-        else ccfma(acc, vj, S[r + c * p.chunk]);            // conj(v_j(i)) P(i,c)
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) p.part[(size_t)b * PS + 1 + c] = acc;
-    }
-    if (!grid_barrier(p.bar, G, p.st)) return;
-    // ---- phase 3: totals, update of the remaining columns, T column j
     for (int c = warp; c < nb; c += PT / 32) {
       cplx acc = mk(0.0, 0.0);
       if (c != j)
-        for (int q = lane; q < G; q += 32) acc = cadd(acc, __ldcg(&p.part[(size_t)q * PS + 1 + c]));
+        for (int q = lane; q < G; q += 32) acc = cadd(acc, __ldcg(&pbuf[(size_t)q * PS + 1 + c]));
       acc = warp_sum(acc);
-      if (lane == 0) wtot[c] = acc;
+      if (lane == 0) wsum[c] = acc;
     }
     __syncthreads();
-    const cplx ctau = cconj(tau);
+    const cplx tau = sh_tau, scal = sh_scal;
+    const double beta = sh_beta;
+    if (t < nb) {
+      const cplx rc = __ldcg(&rw[t]);
+      if (t > j) {  // conj(tau) w_c
+        const cplx wc = cmul(cconj(scal), csub(wsum[t], cscal(beta, rc)));
+        cw[t] = cmul(cconj(tau), wc);
+      } else if (t < j) {  // V(:, t)^H v
+        vv[t] = cmul(scal, csub(wsum[t], cscal(beta, cconj(rc))));
+      }
+    }
+    // ---- the reflector in column j
+    for (int r = t; r < rows; r += PT) {
+      const int gi = r0 + r;
+      if (gi > j) S[r + j * p.chunk] = cmul(S[r + j * p.chunk], scal);
+      else if (gi == j) S[r + j * p.chunk] = mk(beta, 0.0);
+    }
+    if (b == 0 && t == 0) p.tau[j] = tau;
+    __syncthreads();
+    // ---- P(i, c) -= conj(tau) v_i w_c  (c > j, i >= j, v_j = 1)
     for (int i = t; i < rows * nb; i += PT) {
-      int r = i % rows, c = i / rows, gi = r0 + r;
+      const int r = i % rows, c = i / rows, gi = r0 + r;
       if (c <= j || gi < j) continue;
-      cplx vj = (gi == j) ? mk(1.0, 0.0) : S[r + j * p.chunk];
-      // P(i,c) -= conj(tau) v_j(i) w_c
-      S[r + c * p.chunk] = csub(S[r + c * p.chunk], cmul(ctau, cmul(vj, wtot[c])));
+      const cplx vi = (gi == j) ? mk(1.0, 0.0) : S[r + j * p.chunk];
+      S[r + c * p.chunk] = csub(S[r + c * p.chunk], cmul(vi, cw[c]));
     }
     if (b == 0) {
-      // T(0:j, j) = -tau T(0:j,0:j) (V^H v_j);  T(j,j) = tau
+      // T(0:j, j) = -tau T(0:j, 0:j) (V^H v_j);  T(j, j) = tau
       for (int r = t; r < j; r += PT) {
         cplx acc = mk(0.0, 0.0);
-        for (int q = r; q < j; ++q) cfma(acc, p.T[r + q * nb], wtot[q]);
+        for (int q = r; q < j; ++q) cfma(acc, p.T[r + q * nb], vv[q]);
         p.T[r + j * nb] = cscal(-1.0, cmul(tau, acc));
       }
       if (t == 0) p.T[j + j * nb] = tau;
     }
     __syncthreads();
+    if (j + 1 < p.kr) sums(j + 1);
   }
   // write back the panel (R above/on the diagonal, V below) and explicit V
   for (int i = t; i < rows * nb; i += PT) {
@@ -175,7 +202,8 @@ size_t he2hb_ws_bytes(int n, int nb, int num_sms) {
   size_t b = 0;
   b += nn * nb * sizeof(cplx) * 7 + 3 * 256;          // two [V X V], VT
   b += (size_t)nb * nb * sizeof(cplx) * 2 + 2 * 256;  // Y, Z
-  b += (size_t)(num_sms + 1) * (nb + 1) * sizeof(cplx) + 256;
+  b += 2 * (size_t)(num_sms + 1) * (nb + 1) * sizeof(cplx) + 256;  // partial sums, two buffers
+  b += 2 * (size_t)nb * sizeof(cplx) + 256;                         // pivot rows, two buffers
   b += 256 * 2;
   return b;
 }
@@ -193,9 +221,9 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
   cplx* VT = a.take<cplx>((size_t)n * nb);
   cplx* Ys = a.take<cplx>((size_t)nb * nb);
   cplx* Zs = a.take<cplx>((size_t)nb * nb);
-  cplx* part = a.take<cplx>((size_t)(c.num_sms + 1) * (nb + 1));
-  cplx* alpha = a.take<cplx>(1);
-  if (!a.ok() || !VXVb[1]) { a.off = save; return GBHE_EWORKSPACE; }
+  cplx* part = a.take<cplx>(2 * (size_t)(c.num_sms + 1) * (nb + 1));
+  cplx* prow = a.take<cplx>(2 * (size_t)nb);
+  if (!a.ok() || !prow) { a.off = save; return GBHE_EWORKSPACE; }
   GBHE_CUDA(cudaMemsetAsync(tau1, 0, sizeof(cplx) * n, c.st));
   const int npan = (n + nb - 1) / nb;
   GBHE_CUDA(cudaMemsetAsync(T1, 0, sizeof(cplx) * (size_t)npan * nb * nb, c.st));
@@ -220,7 +248,7 @@ int he2hb_run(Ctx& c, int n, int nb, cplx* A, int lda, cplx* T1, cplx* tau1) {
     PanelArgs pa;
     pa.A = A; pa.lda = lda; pa.n = n; pa.k = k; pa.nb = nb; pa.kr = kr; pa.mp = mp; pa.chunk = chunk;
     pa.V = buf; pa.ldv = n; pa.tau = tau1 + k; pa.T = T1 + (size_t)(k / nb) * nb * nb;
-    pa.part = part; pa.alpha = alpha; pa.bar = reinterpret_cast<unsigned*>(c.status + ST_BAR);
+    pa.part = part; pa.row = prow; pa.bar = reinterpret_cast<unsigned*>(c.status + ST_BAR);
     pa.st = c.status;
     void* args[] = {&pa};
     GBHE_CUDA(cudaEventRecord(c.ev_a, c.st));

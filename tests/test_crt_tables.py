@@ -118,8 +118,9 @@ def test_residue_split_replay(T):
     r = fmaf(-rintf(t * pinv), p, t) with pinv = 1/p rounded to float.  Every
     partial sum of t is an integer below 2^23 (so the fma chain is exact, and
     so is the final fma, whose result is an integer), the only rounding is
-    t * pinv; the replay checks that r = v mod p with |r| <= 128 (exact in
-    FP16, and within the bound of the FP32 chunk sums)."""
+    t * pinv; the replay checks that r = v mod p with |r| <= 128 (within
+    the bound of the FP32 chunk sums), and that the device's fold of 128 to
+    -128 (p = 256 only) gives a signed byte congruent to v."""
     rng = np.random.default_rng(3)
     top = 1 << 52
     # largest magnitude that the rounding to 52 bits can produce: (2^53 - 1 + 1) >> 1
@@ -139,6 +140,11 @@ def test_residue_split_replay(T):
             r = t - q * pl
             assert int(np.abs(r).max()) <= 128
             assert np.all((r - sign * mags) % pl == 0)
+            b = np.where(r > 127, r - pl, r)                # the stored signed byte
+            assert int(b.min()) >= -128 and int(b.max()) <= 127
+            assert np.all((b - sign * mags) % pl == 0)
+            if pl % 2:                                      # odd moduli never reach 128
+                assert int(np.abs(r).max()) <= 127
 
 
 def _int160_to_double(C, sc):
@@ -210,7 +216,7 @@ def _crt_ws(m, n, k, cplx):
 
 
 def test_crt_workspace_matches_the_layout(T):
-    """Residue planes 16 x (Re, Im) x rows x K padded to 32 (FP16) for both
+    """Residue planes 16 x (Re, Im) x rows x K padded to 32 (bytes) for both
     operands, output residue bytes in 128 x 64 tiles per modulus and
     component, one exponent per row and column, plus alignment."""
     for m, n, k, cplx in [(1, 1, 1, 1), (128, 64, 32, 0), (129, 65, 33, 1), (4096, 4096, 64, 1),
@@ -218,11 +224,45 @@ def test_crt_workspace_matches_the_layout(T):
         nc = 2 if cplx else 1
         kp = -(-k // 32) * 32
         tiles = -(-m // 128) * -(-n // 64)
-        want = 16 * nc * (m + n) * kp * 2 + tiles * 16 * nc * 128 * 64 + (m + n) * 4 + 4 * 256
+        want = 16 * nc * (m + n) * kp + tiles * 16 * nc * 128 * 64 + (m + n) * 4 + 4 * 256
         rc, got = _crt_ws(m, n, k, cplx)
         assert rc == 0 and got == want, (m, n, k, cplx, got, want)
-    # about 16 GB for one complex product of order 10000 in every dimension
-    assert abs(_crt_ws(10000, 10000, 10000, 1)[1] / 1e9 - 16.1) < 0.1
+    # about 9.7 GB for one complex product of order 10000 in every dimension
+    assert abs(_crt_ws(10000, 10000, 10000, 1)[1] / 1e9 - 9.66) < 0.05
     assert _crt_ws(-1, 1, 1, 1)[0] == -1
     assert _crt_ws(1, -1, 1, 1)[0] == -2
     assert _crt_ws(1, 1, 65537, 1)[0] == -3          # beyond the exactness bound K <= 2^16
+
+
+def _prmt(a, b, sel):
+    """PTX prmt.b32 (default mode): byte i of the result is byte
+    (sel >> 4 i) & 7 of the eight bytes b:a (a the low four)."""
+    src = [(a >> (8 * i)) & 0xFF for i in range(4)] + [(b >> (8 * i)) & 0xFF for i in range(4)]
+    return sum(src[(sel >> (4 * i)) & 7] << (8 * i) for i in range(4))
+
+
+def test_byte_widening_replay():
+    """The product kernels' producers widen 16 stored signed bytes (residues
+    at k .. k+15 of one row) to two FP16 core-matrix rows: each byte is
+    biased by xor 0x80, placed under the exponent bits of 1024 by prmt
+    (0x64uu = 1024 + u in FP16) and 1152 (0x6480) is subtracted.  The replay
+    checks every byte value and the element order of both rows."""
+    one = np.array([0x6480], dtype=np.uint16).view(np.float16)[0]
+    assert float(one) == 1152.0
+    b = np.arange(-128, 128)
+    u = (b & 0xFF) ^ 0x80
+    h = (0x6400 | u).astype(np.uint16).view(np.float16)
+    assert np.all(h.astype(np.float64) == 1024 + u)
+    assert np.all((h - one).astype(np.float64) == b)      # FP16 difference, exact
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        row = rng.integers(-128, 128, 16)
+        words = [int(sum(((int(row[4 * w + i]) & 0xFF) << (8 * i)) for i in range(4))) for w in range(4)]
+        biased = [x ^ 0x80808080 for x in words]
+        out = []
+        for x in biased:
+            for sel in (0x4140, 0x4342):
+                pair = _prmt(x, 0x64646464, sel)
+                halves = np.array([pair & 0xFFFF, pair >> 16], dtype=np.uint16).view(np.float16)
+                out.extend((halves - one).astype(np.float64))
+        assert out == [float(v) for v in row]                 # lo row k..k+7, hi row k+8..k+15
