@@ -54,10 +54,20 @@ def _load_peaks():
 
 PEAKS = _load_peaks()
 
-# DRAM traffic of the product kernels per launch, from one ncu capture of the
-# build it names (dram__bytes_read.sum + dram__bytes_write.sum); None when no
-# capture of the current kernels exists.
-PRODUCT_TRAFFIC = {"bytes_per_launch": None, "source": None}
+# DRAM traffic of the product kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum over every product launch of one solve) per
+# algorithmic contraction flop, from one ncu capture of a smaller solve of
+# the same kernels; scaled to the bench's solve by its algorithmic flops and
+# divided by its live launch count.  None when no capture of the current
+# kernels exists.
+PRODUCT_TRAFFIC = {"bytes_per_algorithmic_flop": None, "source": None}
+
+
+def product_traffic(alg_flops_per_solve, launches_per_solve):
+    r = PRODUCT_TRAFFIC["bytes_per_algorithmic_flop"]
+    if r is None or launches_per_solve <= 0:
+        return None
+    return r * alg_flops_per_solve / launches_per_solve
 
 
 def pm_launches(prof):
@@ -420,7 +430,8 @@ def run_ours(args):
         fp64eq = pd["flops"] / (pd["ms"] * 1e-3) / 1e12
         roof = {"kernel": "k_crt_umma / k_crt_umma_ws (tcgen05.mma kind::f16, FP32 accumulators in TMEM)",
                 "bound": "tensor", "achieved": tr["achieved"], "peak": peak, "unit": "TFLOP/s",
-                "frac": tr["frac"], "traffic": PRODUCT_TRAFFIC["bytes_per_launch"],
+                "frac": tr["frac"],
+                "traffic": product_traffic(tr["algorithmic_fp64_flops_per_solve"], tr["launches_per_solve"]),
                 "traffic_source": PRODUCT_TRAFFIC["source"],
                 "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json; fp16 runs at the bf16 rate)",
                 "launches": pm_launches(prof), "ms": prof["crt_mma"]["ms"],
@@ -694,7 +705,8 @@ def run_q2_case(args):
         print(json.dumps({"q2_case": path, "saved": True, "n": n, "nb": nb}))
         return 0
     z = np.load(path)
-    A, Z = G.colmajor(z["A"], dev), G.colmajor(z["Z"], dev)
+    m = max(1, inputs.fraction_iu(n, args.frac))  # --frac < 0.8 keeps Q2 on the eigenvectors (no explicit Q2)
+    A, Z = G.colmajor(z["A"], dev), G.colmajor(np.ascontiguousarray(z["Z"][:, :m]), dev)
     T1, V2, tau2 = (torch.from_numpy(z[k]).to(dev) for k in ("T1", "V2", "tau2"))
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -59,3 +59,14 @@ def test_contraction_flops_and_tensor_roofline():
     assert abs(tr["frac"] - tr["achieved"] / 1941.1) < 1e-12
     assert abs(tr["executed_fp64_flops_per_solve"] - 4.69e13) < 1.0
     assert bench.tensor_roofline({"crt_mma": {"ms": 0.0, "flops": 0.0, "launches": 0}}, n, m, 1, 1.0) is None
+
+
+def test_product_traffic_scaling(monkeypatch):
+    """Traffic per launch = bytes per algorithmic flop (from the capture of a
+    smaller solve) x the solve's algorithmic flops / its launches; None
+    without a capture of the current kernels."""
+    monkeypatch.setitem(bench.PRODUCT_TRAFFIC, "bytes_per_algorithmic_flop", None)
+    assert bench.product_traffic(3e13, 5000) is None
+    monkeypatch.setitem(bench.PRODUCT_TRAFFIC, "bytes_per_algorithmic_flop", 0.1)
+    assert bench.product_traffic(3e13, 5000) == pytest.approx(6e8)
+    assert bench.product_traffic(3e13, 0) is None
