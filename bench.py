@@ -60,7 +60,11 @@ PEAKS = _load_peaks()
 # the same kernels; scaled to the bench's solve by its algorithmic flops and
 # divided by its live launch count.  None when no capture of the current
 # kernels exists.
-PRODUCT_TRAFFIC = {"bytes_per_algorithmic_flop": None, "source": None}
+PRODUCT_TRAFFIC = {"bytes_per_algorithmic_flop": 0.0543,
+                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all 1628 product launches of "
+                             "one n=4096 solve (114.4 GB / 2.107e12 algorithmic flops), product kernels of commit "
+                             "222c44f; scaled by this solve's algorithmic flops per launch "
+                             "(profiles/crt_products_traffic_n4096.md)"}
 
 
 def product_traffic(alg_flops_per_solve, launches_per_solve):
