@@ -67,9 +67,14 @@ PRODUCT_TRAFFIC = {"bytes_per_algorithmic_flop": 0.0543,
                              "(profiles/crt_products_traffic_n4096.md)"}
 
 
-def product_traffic(alg_flops_per_solve, launches_per_solve):
+def product_traffic(alg_flops_per_solve, launches_per_solve, n=None, m=None):
+    """Scaled traffic per product launch; None without a capture, or for a
+    solve whose back-transform takes the other Q2 path than the captured one
+    (the capture formed Q2 explicitly: all eigenvectors, m >= 0.8 n)."""
     r = PRODUCT_TRAFFIC["bytes_per_algorithmic_flop"]
     if r is None or launches_per_solve <= 0:
+        return None
+    if n is not None and m is not None and 5 * m < 4 * n:
         return None
     return r * alg_flops_per_solve / launches_per_solve
 
@@ -435,7 +440,7 @@ def run_ours(args):
         roof = {"kernel": "k_crt_umma / k_crt_umma_ws (tcgen05.mma kind::f16, FP32 accumulators in TMEM)",
                 "bound": "tensor", "achieved": tr["achieved"], "peak": peak, "unit": "TFLOP/s",
                 "frac": tr["frac"],
-                "traffic": product_traffic(tr["algorithmic_fp64_flops_per_solve"], tr["launches_per_solve"]),
+                "traffic": product_traffic(tr["algorithmic_fp64_flops_per_solve"], tr["launches_per_solve"], n, m),
                 "traffic_source": PRODUCT_TRAFFIC["source"],
                 "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json; fp16 runs at the bf16 rate)",
                 "launches": pm_launches(prof), "ms": prof["crt_mma"]["ms"],

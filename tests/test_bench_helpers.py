@@ -70,3 +70,5 @@ def test_product_traffic_scaling(monkeypatch):
     monkeypatch.setitem(bench.PRODUCT_TRAFFIC, "bytes_per_algorithmic_flop", 0.1)
     assert bench.product_traffic(3e13, 5000) == pytest.approx(6e8)
     assert bench.product_traffic(3e13, 0) is None
+    assert bench.product_traffic(3e13, 5000, 10000, 10000) == pytest.approx(6e8)
+    assert bench.product_traffic(3e13, 5000, 10000, 2500) is None     # the other Q2 path
