@@ -7,9 +7,15 @@
 // sweep the steps act on disjoint rows (they commute); H(s+1, .) overlaps
 // H(s, .) only for equal or neighbouring steps.  Grouping nb consecutive
 // sweeps, the valid order is: groups from last to first; inside a group step
-// j ascending; inside (group, j) sweeps descending.  Each CTA owns a slab of
-// SLAB columns of X and walks all reflectors in that order, keeping the
-// (2nb-1)-row window of the current (group, j) in shared memory.
+// j ascending; inside (group, j) sweeps descending.  With the tensor-core
+// engine the reflectors of one (group, j) form a block reflector, two groups'
+// blocks are merged, and the merged blocks are applied in wavefront steps as
+// batched products (apply_q2_blocks); when most eigenvectors are wanted the
+// same blocks are applied to the identity instead, each only to the columns
+// it can reach, and X = Q2 Z follows as one product.  Otherwise (the FP64
+// engine, or nb beyond the block path) each CTA owns a slab of SLAB columns
+// of X and walks all reflectors in that order, keeping the (2nb-1)-row window
+// of the current (group, j) in shared memory (k_apply_q2).
 //
 // Q1 (panel block reflectors of stage 1).  Q1 = Q_0 Q_1 ... with
 // Q_p = I - V_p T_p V_p^H on rows p*nb+nb .. n-1, applied last panel first,
